@@ -1,0 +1,191 @@
+/*
+ * eslbm.h -- C ABI of the GB300 (sm_103a) implementation of the fourth-order,
+ * entropy-stable, vectorial lattice Boltzmann scheme of Bellotti, Helluy and
+ * Navoret, "Fourth-order entropy-stable lattice Boltzmann schemes for
+ * hyperbolic systems" (arXiv 2403.13406).
+ *
+ * The calls follow the paper's statement of the problem:
+ *   - initialise the distributions at equilibrium from conserved fields
+ *     (Section 3.1: data taken at equilibrium, f_k = f^eq_k(u0));
+ *   - run n composite steps Phi(dt) = psi(dt/6)^4 psi(-dt/3) psi(dt/6)^4 of the
+ *     basic brick psi(dt) = T(dt/4) R T(dt/2) R T(dt/4) (eqs. splittingToUse
+ *     and basicBrickSplitting), dt = 24 kappa dx / V (Section 2.3), with the
+ *     relaxation R_omega of eq. relaxationDiscretizationOmega and either a
+ *     fixed omega or the per-cell entropic omega of eq. variableOmegaProblem
+ *     (Section 4);
+ *   - read back the conserved moments u = sum_k f_k and the total microscopic
+ *     and macroscopic entropies (Section 4).
+ *
+ * Conventions
+ *   - Velocity sets (Section 1.2): D1Q2 with velocities (+V, -V); D2Q4 with
+ *     (+V,0), (0,+V), (-V,0), (0,-V), in that order.
+ *   - Distributions are stored structure-of-arrays: plane (k*M + m) holds the
+ *     m-th conserved component of population k for every cell, cells row-major
+ *     with x fastest (cell = y*nx + x).  Conserved fields use M planes with the
+ *     same cell order.  Host-side fields are always double precision; device
+ *     state is float or double according to eslbm_config.precision.
+ *   - The grid is periodic with cells at x_j = j dx.
+ *   - Memory: the caller owns every buffer.  The library never allocates device
+ *     memory: eslbm_create receives two state buffers (ping-pong) and a
+ *     workspace, sized by eslbm_query.  Buffers passed with on_device = 0 are
+ *     host buffers; the call then copies through the spare state buffer and
+ *     synchronizes the stream before it returns.  Device buffers are used
+ *     asynchronously on the handle's stream.
+ *   - Errors: nothing throws across the ABI.  Every call returns an
+ *     eslbm_status; eslbm_last_error(h) describes the last failure of h.
+ */
+#ifndef ESLBM_H
+#define ESLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ESLBM_ABI_VERSION 1
+
+typedef enum {
+    ESLBM_OK = 0,
+    ESLBM_ERR_ARG = 1,          /* invalid argument (null pointer, size, enum value) */
+    ESLBM_ERR_DOMAIN = 2,       /* data outside the convexity / sub-characteristic domain */
+    ESLBM_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    ESLBM_ERR_NAN = 4,          /* non-finite values in the input or the state */
+    ESLBM_ERR_UNSUPPORTED = 5,  /* valid but not implemented combination */
+    ESLBM_WARN_OMEGA_FALLBACK = 100 /* some cells had no entropic root; omega = 1 was used */
+} eslbm_status;
+
+/* Conservation laws of Section 1.2.  LINEAR: phi^j = a_j u (Examples 1, 4).
+   BURGERS: phi^j = c_j u^2/2 (Example 2; Section 3.3 uses c = (1, 3/5)).
+   SHALLOW_WATER: (h, hu[, hv]) with gravity g (Example 3).  EULER: (rho, rho u,
+   rho v, E) with gamma-law pressure (Section 6.3), fixed omega only. */
+enum { ESLBM_LINEAR = 0, ESLBM_BURGERS = 1, ESLBM_SHALLOW_WATER = 2, ESLBM_EULER = 3 };
+enum { ESLBM_FP32 = 0, ESLBM_FP64 = 1 };
+enum { ESLBM_OMEGA_FIXED = 0, ESLBM_OMEGA_ENTROPIC = 1 };
+/* Schemes (I)-(IV) of Section 6.1; PLAIN is the standard scheme R T(kappa dx/V)
+   of Section 2.1 (one stage per step); B is scheme (B) of Section 6.3,
+   R_1 T(dt/4) R T(dt/2) R T(dt/4) with dt = 4 kappa dx / V. */
+enum { ESLBM_SCHEME_I = 1, ESLBM_SCHEME_II = 2, ESLBM_SCHEME_III = 3, ESLBM_SCHEME_IV = 4,
+       ESLBM_SCHEME_PLAIN = 5, ESLBM_SCHEME_B = 6 };
+/* Relaxation kinds for eslbm_relax: the scheme's main relaxation (fixed omega
+   or entropic omega) or the projection on the equilibrium R_1 (Section 6.1). */
+enum { ESLBM_RELAX_MAIN = 0, ESLBM_RELAX_PROJECT = 1 };
+
+typedef struct {
+    int32_t dim;        /* 1 (D1Q2) or 2 (D2Q4) */
+    int32_t system;     /* ESLBM_LINEAR, ESLBM_BURGERS, ESLBM_SHALLOW_WATER, ESLBM_EULER */
+    int32_t precision;  /* ESLBM_FP32 or ESLBM_FP64: storage and arithmetic of the distributions */
+    int32_t omega_mode; /* ESLBM_OMEGA_FIXED or ESLBM_OMEGA_ENTROPIC */
+    int32_t scheme;     /* ESLBM_SCHEME_* */
+    int32_t kappa;      /* shift unit V dt / (24 dx) >= 1 (Section 2.3; the paper uses 1) */
+    int64_t nx, ny;     /* cells per direction; ny = 1 when dim = 1 */
+    double V;           /* lattice velocity V > 0 */
+    double omega;       /* fixed relaxation parameter (fixed mode), e.g. 2 */
+    double a[2];        /* linear transport velocity */
+    double c[2];        /* Burgers flux coefficients */
+    double g;           /* gravity (shallow water) */
+    double gamma;       /* ratio of specific heats (Euler) */
+    double t_max;       /* entropic mode: omega - 1 is searched in [0, t_max]; 0 -> 3 */
+    int32_t diagnostics;/* 1: count per-cell entropy increases and track omega min/max */
+    int32_t reserved;
+} eslbm_config;
+
+typedef struct {
+    int64_t q;               /* velocities: 2 (D1Q2) or 4 (D2Q4) */
+    int64_t M;               /* conserved components */
+    int64_t planes;          /* q * M */
+    int64_t ncell;           /* nx * ny */
+    uint64_t state_bytes;    /* bytes of one distribution buffer (planes * ncell * element) */
+    uint64_t workspace_bytes;/* bytes of the workspace */
+    int64_t stages_per_step; /* fused relax-plus-shift stages per step of the scheme */
+    int64_t step_cells;      /* lattice time of one step in units of dx / V (24 kappa for I-IV) */
+} eslbm_sizes;
+
+typedef struct {
+    uint64_t relaxations;        /* cell relaxations since the last reset */
+    uint64_t fallbacks;          /* cells that used omega = 1 (no entropic root) */
+    uint64_t entropy_increases;  /* cells whose Sigma increased (diagnostics = 1) */
+    double omega_min, omega_max; /* range of omega used (diagnostics = 1) */
+} eslbm_diagnostics;
+
+typedef struct eslbm_handle eslbm_handle;
+
+/* Version of this ABI (ESLBM_ABI_VERSION). */
+int32_t eslbm_abi_version(void);
+
+/* Human-readable name of a status code; never NULL. */
+const char *eslbm_status_string(eslbm_status s);
+
+/* Sizes of the buffers for cfg.  Validates cfg (ESLBM_ERR_ARG on a bad
+   field, ESLBM_ERR_UNSUPPORTED for entropic Euler). */
+eslbm_status eslbm_query(const eslbm_config *cfg, eslbm_sizes *out);
+
+/* Create a handle.  f_a, f_b: device buffers of sizes.state_bytes each (16-byte
+   aligned); workspace: device buffer of sizes.workspace_bytes; stream: a
+   cudaStream_t (NULL = legacy default stream).  The buffers stay owned by the
+   caller and must outlive the handle.  The handle is allocated on the host. */
+eslbm_status eslbm_create(const eslbm_config *cfg, void *f_a, void *f_b, void *workspace,
+                          void *stream, eslbm_handle **out);
+
+/* Release the handle (not the buffers).  Safe on NULL. */
+eslbm_status eslbm_destroy(eslbm_handle *h);
+
+/* Switch the stream used by later calls. */
+eslbm_status eslbm_set_stream(eslbm_handle *h, void *stream);
+
+/* Message describing the last failure on h (empty if none); never NULL. */
+const char *eslbm_last_error(const eslbm_handle *h);
+
+/* f_k = f^eq_k(u0) in every cell (Section 3.1).  u0: M double planes of ncell
+   cells.  Checks the convexity / sub-characteristic domain of Section 1.2 on the
+   device (synchronizes) and returns ESLBM_ERR_DOMAIN (state untouched) if a cell
+   violates it, ESLBM_ERR_NAN for non-finite input.  Resets the pending shift. */
+eslbm_status eslbm_init_equilibrium(eslbm_handle *h, const double *u0, int32_t u0_on_device);
+
+/* Set the distributions directly (q*M double planes, rounded to the storage
+   precision), e.g. off-equilibrium data (Section 6.2).  No domain check. */
+eslbm_status eslbm_init_distributions(eslbm_handle *h, const double *f0, int32_t on_device);
+
+/* Advance n composite steps of the configured scheme (eq. splittingToUse for
+   scheme I).  Asynchronous on the stream; adjacent transports are merged into
+   one pull-shift per fused stage and the trailing shift of the last step is
+   kept pending until the next stage or readback. */
+eslbm_status eslbm_step(eslbm_handle *h, int64_t n);
+
+/* Apply the transport T(s) (eq. transportPhase, s cells along each
+   population's velocity, negative s reverses it): recorded as a pending shift
+   and folded into the next stage or readback (a pure permutation). */
+eslbm_status eslbm_transport(eslbm_handle *h, int64_t s);
+
+/* One relaxation sweep (eq. relaxationDiscretizationOmega) of the given kind,
+   fused with the pending shift. */
+eslbm_status eslbm_relax(eslbm_handle *h, int32_t kind);
+
+/* Conserved moments u = sum_k f_k (M double planes) of the current state. */
+eslbm_status eslbm_read_moments(eslbm_handle *h, double *u_out, int32_t on_device);
+
+/* Distributions in logical order (q*M double planes, pending shift applied). */
+eslbm_status eslbm_read_distributions(eslbm_handle *h, double *f_out, int32_t on_device);
+
+/* Totals reduced in double precision with a fixed order (deterministic):
+   out[0] = sum_x Sigma(f(x)) (total microscopic entropy, Section 4),
+   out[1] = sum_x S(u(x)) (total entropy of the moments),
+   out[2 .. 2+M-1] = sum_x u_m(x) (conserved totals).
+   Entropies are NaN for EULER (no kinetic entropy is defined). */
+eslbm_status eslbm_read_totals(eslbm_handle *h, double *out, int32_t on_device);
+
+/* Counters accumulated by the stage kernels since the last reset (synchronizes).
+   Returns ESLBM_WARN_OMEGA_FALLBACK when fallbacks > 0. */
+eslbm_status eslbm_get_diagnostics(eslbm_handle *h, eslbm_diagnostics *out);
+eslbm_status eslbm_reset_diagnostics(eslbm_handle *h);
+
+/* Capture the launches of one step (two for an odd number of stages) in a CUDA
+   graph and replay it inside eslbm_step (enable = 1), or launch directly
+   (enable = 0, the default). */
+eslbm_status eslbm_use_graph(eslbm_handle *h, int32_t enable);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ESLBM_H */

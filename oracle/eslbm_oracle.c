@@ -614,7 +614,9 @@ static int brick_iv(const or_model *m, double *f, long num, long den, or_stats *
 
 long or_step_length(const or_model *m, int scheme)
 {
-    return scheme == OR_SCHEME_B ? 4L * m->kappa : 24L * m->kappa;
+    if (scheme == OR_SCHEME_B) return 4L * m->kappa;
+    if (scheme == OR_SCHEME_PLAIN) return (long)m->kappa;
+    return 24L * m->kappa;
 }
 
 int or_composite_steps(const or_model *m, double *f, int scheme, long nsteps, or_stats *st)
@@ -646,11 +648,9 @@ int or_composite_steps(const or_model *m, double *f, int scheme, long nsteps, or
             if (scheme == OR_SCHEME_II) or_relax(m, f, OR_R_PROJECT, st);
             break;
         }
-        case OR_SCHEME_PLAIN: /* (R T(dt/24))^24 of Section 3.1 */
-            for (int r = 0; r < 24; ++r) {
-                if (or_transport(m, f, m->kappa)) return -1;
-                or_relax(m, f, OR_R_MAIN, st);
-            }
+        case OR_SCHEME_PLAIN: /* the standard scheme R T(kappa dx / V) of Section 2.1 */
+            if (or_transport(m, f, m->kappa)) return -1;
+            or_relax(m, f, OR_R_MAIN, st);
             break;
         case OR_SCHEME_B: /* R_1 T(dt/4) R_2 T(dt/2) R_2 T(dt/4), dt = 4 dx / V (Section 6.3) */
             if (or_transport(m, f, m->kappa)) return -1;

@@ -32,8 +32,9 @@ enum { OR_OMEGA_FIXED = 0, OR_OMEGA_ENTROPIC = 1 };
 /* which relaxation a stage applies: the scheme's main one (fixed omega or
    entropic omega), or the projection on the equilibrium R_1 (Section 6.1) */
 enum { OR_R_MAIN = 0, OR_R_PROJECT = 1 };
-/* composite schemes: I-IV of Section 6.1, the plain second-order lattice
-   Boltzmann scheme (R T(dt/24))^24 of Section 3.1, and scheme (B) of
+/* composite schemes: I-IV of Section 6.1, the standard second-order lattice
+   Boltzmann scheme R T(kappa dx / V) of Section 2.1 (one stage per step; 24
+   of its steps span one composite step, Section 3.1), and scheme (B) of
    Section 6.3 */
 enum { OR_SCHEME_I = 1, OR_SCHEME_II = 2, OR_SCHEME_III = 3, OR_SCHEME_IV = 4,
        OR_SCHEME_PLAIN = 5, OR_SCHEME_B = 6 };

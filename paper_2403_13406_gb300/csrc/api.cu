@@ -1,0 +1,581 @@
+// api.cu -- host implementation of the C ABI declared in include/eslbm.h.
+//
+// The composite step is kept as the paper's operator list (transports T(s) and
+// relaxations R) built from the rational composition weights; a small
+// interpreter merges adjacent transports into the pull-shift of the next fused
+// stage and carries the trailing transport as a pending shift, so a run of n
+// steps of scheme I is T(1), then 18 n fused stages, then T(1) at readback.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/eslbm.h"
+#include "launch.h"
+
+using namespace eslbm;
+
+namespace {
+
+struct Op {
+    bool relax;
+    int64_t shift;
+    int kind;
+};
+
+constexpr size_t kCountersBytes = 256;
+
+// Operator list of one step, in application order (operators compose right to
+// left in the paper's formulas).
+std::vector<Op> scheme_ops(int scheme, int64_t kappa)
+{
+    std::vector<Op> ops;
+    auto T = [&](int64_t s) { ops.push_back({false, s, 0}); };
+    auto R = [&](int kind) { ops.push_back({true, 0, kind}); };
+    // psi(coef dt) = T(coef dt/4) R T(coef dt/2) R T(coef dt/4), dt = 24 kappa dx / V
+    // (eq. basicBrickSplitting); T(coef dt/4) shifts 6 kappa coef cells.
+    auto brick = [&](int64_t q4) {
+        T(q4);
+        R(KIND_MAIN);
+        T(2 * q4);
+        R(KIND_MAIN);
+        T(q4);
+    };
+    // Scheme (IV): R_1 T R_2 T R_1 T R_2 T with quarter transports (Section 6.1)
+    auto brick_iv = [&](int64_t q4) {
+        for (int half = 0; half < 2; ++half) {
+            T(q4);
+            R(KIND_MAIN);
+            T(q4);
+            R(KIND_PROJECT);
+        }
+    };
+    switch (scheme) {
+    case ESLBM_SCHEME_I:
+    case ESLBM_SCHEME_II:
+    case ESLBM_SCHEME_III:
+    case ESLBM_SCHEME_IV: {
+        // eq. splittingToUse: psi(dt/6)^4 psi(-dt/3) psi(dt/6)^4 (n = 4, alpha = 1/6,
+        // beta = -1/3 solve eqs. fourtOrderConditionOne/Two)
+        const int64_t n_outer = 4, a_num = 1, a_den = 6, b_num = -1, b_den = 3;
+        const int64_t qa = 6 * kappa * a_num / a_den, qb = 6 * kappa * b_num / b_den;
+        for (int part = 0; part < 3; ++part) {
+            const int64_t reps = part == 1 ? 1 : n_outer;
+            const int64_t q4 = part == 1 ? qb : qa;
+            for (int64_t r = 0; r < reps; ++r) {
+                if (scheme == ESLBM_SCHEME_IV) brick_iv(q4);
+                else brick(q4);
+                if (scheme == ESLBM_SCHEME_III) R(KIND_PROJECT);
+            }
+        }
+        if (scheme == ESLBM_SCHEME_II) R(KIND_PROJECT);
+        break;
+    }
+    case ESLBM_SCHEME_PLAIN:  // R T(kappa dx/V), Section 2.1
+        T(kappa);
+        R(KIND_MAIN);
+        break;
+    case ESLBM_SCHEME_B:  // R_1 T(dt/4) R T(dt/2) R T(dt/4), dt = 4 kappa dx / V, Section 6.3
+        T(kappa);
+        R(KIND_MAIN);
+        T(2 * kappa);
+        R(KIND_MAIN);
+        T(kappa);
+        R(KIND_PROJECT);
+        break;
+    }
+    return ops;
+}
+
+int64_t step_cells(int scheme, int64_t kappa)
+{
+    if (scheme == ESLBM_SCHEME_PLAIN) return kappa;
+    if (scheme == ESLBM_SCHEME_B) return 4 * kappa;
+    return 24 * kappa;
+}
+
+int family_of(const eslbm_config &c)
+{
+    switch (c.system) {
+    case ESLBM_LINEAR: return c.dim == 1 ? FAM_LINEAR1 : FAM_LINEAR2;
+    case ESLBM_BURGERS: return c.dim == 1 ? FAM_BURGERS1 : FAM_BURGERS2;
+    case ESLBM_SHALLOW_WATER: return c.dim == 1 ? FAM_SW1 : FAM_SW2;
+    default: return FAM_EULER2;
+    }
+}
+
+int64_t num_M(const eslbm_config &c)
+{
+    if (c.system == ESLBM_SHALLOW_WATER) return c.dim + 1;
+    if (c.system == ESLBM_EULER) return 4;
+    return 1;
+}
+
+eslbm_status validate(const eslbm_config *c)
+{
+    if (!c) return ESLBM_ERR_ARG;
+    if (c->dim != 1 && c->dim != 2) return ESLBM_ERR_ARG;
+    if (c->system < ESLBM_LINEAR || c->system > ESLBM_EULER) return ESLBM_ERR_ARG;
+    if (c->precision != ESLBM_FP32 && c->precision != ESLBM_FP64) return ESLBM_ERR_ARG;
+    if (c->omega_mode != ESLBM_OMEGA_FIXED && c->omega_mode != ESLBM_OMEGA_ENTROPIC) return ESLBM_ERR_ARG;
+    if (c->scheme < ESLBM_SCHEME_I || c->scheme > ESLBM_SCHEME_B) return ESLBM_ERR_ARG;
+    if (c->kappa < 1 || c->kappa > 1024) return ESLBM_ERR_ARG;
+    if (c->nx < 1 || c->ny < 1 || (c->dim == 1 && c->ny != 1)) return ESLBM_ERR_ARG;
+    if (c->dim == 2 && c->ny > 65535) return ESLBM_ERR_ARG;  // one grid row of blocks per cell row
+    if (c->nx > (int64_t(1) << 40) || c->nx * c->ny > (int64_t(1) << 40)) return ESLBM_ERR_ARG;
+    if (!(c->V > 0.0) || !std::isfinite(c->V)) return ESLBM_ERR_ARG;
+    if (c->omega_mode == ESLBM_OMEGA_FIXED && !(std::isfinite(c->omega))) return ESLBM_ERR_ARG;
+    if (c->t_max < 0.0 || !std::isfinite(c->t_max)) return ESLBM_ERR_ARG;
+    if (c->system == ESLBM_SHALLOW_WATER && !(c->g > 0.0)) return ESLBM_ERR_ARG;
+    if (c->system == ESLBM_EULER) {
+        if (c->dim != 2) return ESLBM_ERR_UNSUPPORTED;
+        if (!(c->gamma > 1.0)) return ESLBM_ERR_ARG;
+        if (c->omega_mode == ESLBM_OMEGA_ENTROPIC) return ESLBM_ERR_UNSUPPORTED;
+    }
+    if (c->system == ESLBM_LINEAR) {  // sub-characteristic condition (Examples 1 and 4)
+        const double lim = c->dim == 1 ? c->V : 0.5 * c->V;
+        for (int j = 0; j < c->dim; ++j)
+            if (!(std::fabs(c->a[j]) < lim)) return ESLBM_ERR_DOMAIN;
+    }
+    return ESLBM_OK;
+}
+
+}  // namespace
+
+struct eslbm_handle {
+    eslbm_config cfg;
+    eslbm_sizes sz;
+    int family;
+    bool fp64;
+    void *f[2];
+    int cur;
+    char *ws;
+    cudaStream_t stream;
+    int64_t pending;
+    Params P;
+    std::vector<Op> ops;
+    uint64_t relaxations;
+    std::string err;
+    // graph replay of `graph_steps` steps entered with (graph_pending, graph_cur)
+    bool use_graph;
+    cudaGraphExec_t gexec;
+    int64_t graph_pending;
+    int graph_cur;
+    int graph_steps;
+    int graph_cur_after;
+    int64_t graph_pending_after;
+
+    Counters *counters() { return reinterpret_cast<Counters *>(ws); }
+    double *partials() { return reinterpret_cast<double *>(ws + kCountersBytes); }
+    double *totals_out()
+    {
+        return reinterpret_cast<double *>(ws + kCountersBytes + sizeof(double) * 6 * (size_t)totals_blocks());
+    }
+    void *spare() { return f[1 - cur]; }
+};
+
+namespace {
+
+eslbm_status fail(eslbm_handle *h, eslbm_status s, const std::string &msg)
+{
+    if (h) h->err = msg;
+    return s;
+}
+
+eslbm_status cuda_fail(eslbm_handle *h, cudaError_t e, const char *where)
+{
+    return fail(h, ESLBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                     \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+    } while (0)
+
+// pull offsets that apply a transport by s cells to every population
+Shift make_shift(const eslbm_handle *h, int64_t s)
+{
+    Shift sh;
+    const int q = (int)h->sz.q;
+    for (int k = 0; k < 4; ++k) sh.roff[k] = 0;
+    for (int k = 0; k < q; ++k) {
+        const int axis = h->cfg.dim == 1 ? 0 : (k & 1);
+        const int sign = h->cfg.dim == 1 ? (k == 0 ? 1 : -1) : (k < 2 ? 1 : -1);
+        const int64_t n = axis == 0 ? h->cfg.nx : h->cfg.ny;
+        int64_t r = (-(int64_t)sign * s) % n;  // value at x comes from x - sign * s
+        if (r < 0) r += n;
+        sh.roff[k] = r;
+    }
+    return sh;
+}
+
+eslbm_status launch_one_stage(eslbm_handle *h, int64_t shift, int kind)
+{
+    StageLaunch L;
+    L.fin = h->f[h->cur];
+    L.fout = h->f[1 - h->cur];
+    L.nx = h->cfg.nx;
+    L.ny = h->cfg.ny;
+    L.ncell = h->sz.ncell;
+    L.sh = make_shift(h, shift);
+    L.kind = kind;
+    L.cnt = h->counters();
+    L.P = h->P;
+    L.stream = h->stream;
+    const bool entropic = h->cfg.omega_mode == ESLBM_OMEGA_ENTROPIC;
+    CK(launch_stage(h->family, h->fp64, entropic, h->cfg.diagnostics != 0, L), "stage launch");
+    h->cur = 1 - h->cur;
+    h->relaxations += (uint64_t)h->sz.ncell;
+    return ESLBM_OK;
+}
+
+eslbm_status run_ops(eslbm_handle *h)
+{
+    for (const Op &op : h->ops) {
+        if (!op.relax) {
+            h->pending += op.shift;
+            continue;
+        }
+        eslbm_status s = launch_one_stage(h, h->pending, op.kind);
+        if (s != ESLBM_OK) return s;
+        h->pending = 0;
+    }
+    return ESLBM_OK;
+}
+
+eslbm_status capture_graph(eslbm_handle *h)
+{
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    const int64_t pend0 = h->pending;
+    const int cur0 = h->cur;
+    const uint64_t rel0 = h->relaxations;
+    const int nsteps = (h->sz.stages_per_step % 2 == 0) ? 1 : 2;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    eslbm_status s = ESLBM_OK;
+    for (int i = 0; i < nsteps && s == ESLBM_OK; ++i) s = run_ops(h);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    h->graph_cur_after = h->cur;
+    h->graph_pending_after = h->pending;
+    h->pending = pend0;
+    h->cur = cur0;
+    h->relaxations = rel0;
+    if (s != ESLBM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+    h->graph_pending = pend0;
+    h->graph_cur = cur0;
+    h->graph_steps = nsteps;
+    return ESLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t eslbm_abi_version(void) { return ESLBM_ABI_VERSION; }
+
+const char *eslbm_status_string(eslbm_status s)
+{
+    switch (s) {
+    case ESLBM_OK: return "ok";
+    case ESLBM_ERR_ARG: return "invalid argument";
+    case ESLBM_ERR_DOMAIN: return "outside the convexity / sub-characteristic domain";
+    case ESLBM_ERR_CUDA: return "CUDA error";
+    case ESLBM_ERR_NAN: return "non-finite values";
+    case ESLBM_ERR_UNSUPPORTED: return "unsupported combination";
+    case ESLBM_WARN_OMEGA_FALLBACK: return "entropic omega fell back to the projection in some cells";
+    }
+    return "unknown status";
+}
+
+eslbm_status eslbm_query(const eslbm_config *cfg, eslbm_sizes *out)
+{
+    if (!out) return ESLBM_ERR_ARG;
+    eslbm_status s = validate(cfg);
+    if (s != ESLBM_OK) return s;
+    eslbm_sizes z;
+    z.q = cfg->dim == 1 ? 2 : 4;
+    z.M = num_M(*cfg);
+    z.planes = z.q * z.M;
+    z.ncell = cfg->nx * cfg->ny;
+    z.state_bytes = (uint64_t)z.planes * (uint64_t)z.ncell * (cfg->precision == ESLBM_FP64 ? 8u : 4u);
+    z.workspace_bytes = kCountersBytes + sizeof(double) * 6 * (uint64_t)totals_blocks() + 256;
+    int64_t stages = 0;
+    for (const Op &op : scheme_ops(cfg->scheme, cfg->kappa)) stages += op.relax ? 1 : 0;
+    z.stages_per_step = stages;
+    z.step_cells = step_cells(cfg->scheme, cfg->kappa);
+    *out = z;
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_create(const eslbm_config *cfg, void *f_a, void *f_b, void *workspace, void *stream,
+                          eslbm_handle **out)
+{
+    if (!out) return ESLBM_ERR_ARG;
+    *out = nullptr;
+    eslbm_sizes sz;
+    eslbm_status s = eslbm_query(cfg, &sz);
+    if (s != ESLBM_OK) return s;
+    if (!f_a || !f_b || !workspace || f_a == f_b) return ESLBM_ERR_ARG;
+    if (((uintptr_t)f_a | (uintptr_t)f_b | (uintptr_t)workspace) & 15u) return ESLBM_ERR_ARG;
+    eslbm_handle *h = new (std::nothrow) eslbm_handle();
+    if (!h) return ESLBM_ERR_ARG;
+    h->cfg = *cfg;
+    h->sz = sz;
+    h->family = family_of(*cfg);
+    h->fp64 = cfg->precision == ESLBM_FP64;
+    h->f[0] = f_a;
+    h->f[1] = f_b;
+    h->cur = 0;
+    h->ws = (char *)workspace;
+    h->stream = (cudaStream_t)stream;
+    h->pending = 0;
+    h->P.V = cfg->V;
+    h->P.a[0] = cfg->a[0];
+    h->P.a[1] = cfg->a[1];
+    h->P.c[0] = cfg->c[0];
+    h->P.c[1] = cfg->c[1];
+    h->P.g = cfg->g;
+    h->P.gamma = cfg->gamma;
+    h->P.omega = cfg->omega;
+    h->P.t_max = cfg->t_max > 0.0 ? cfg->t_max : 3.0;
+    if (cfg->omega_mode == ESLBM_OMEGA_ENTROPIC && cfg->system == ESLBM_LINEAR) h->P.omega = 2.0;
+    h->ops = scheme_ops(cfg->scheme, cfg->kappa);
+    h->relaxations = 0;
+    h->use_graph = false;
+    h->gexec = nullptr;
+    h->graph_steps = 0;
+    s = eslbm_reset_diagnostics(h);
+    if (s != ESLBM_OK) {
+        delete h;
+        return s;
+    }
+    *out = h;
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_destroy(eslbm_handle *h)
+{
+    if (!h) return ESLBM_OK;
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    delete h;
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_set_stream(eslbm_handle *h, void *stream)
+{
+    if (!h) return ESLBM_ERR_ARG;
+    h->stream = (cudaStream_t)stream;
+    return ESLBM_OK;
+}
+
+const char *eslbm_last_error(const eslbm_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+eslbm_status eslbm_init_equilibrium(eslbm_handle *h, const double *u0, int32_t u0_on_device)
+{
+    if (!h || !u0) return fail(h, ESLBM_ERR_ARG, "null argument");
+    const size_t ubytes = sizeof(double) * (size_t)h->sz.M * (size_t)h->sz.ncell;
+    const double *src = u0;
+    if (!u0_on_device) {
+        CK(cudaMemcpyAsync(h->spare(), u0, ubytes, cudaMemcpyHostToDevice, h->stream), "copy u0");
+        src = (const double *)h->spare();
+    }
+    Counters *c = h->counters();
+    CK(cudaMemsetAsync(&c->domain_violations, 0, 2 * sizeof(unsigned long long), h->stream), "clear flags");
+    CK(launch_init_eq(h->family, h->fp64, src, h->f[h->cur], h->sz.ncell, h->P, c, h->stream), "init launch");
+    unsigned long long flags[2];
+    CK(cudaMemcpyAsync(flags, &c->domain_violations, sizeof(flags), cudaMemcpyDeviceToHost, h->stream),
+       "read flags");
+    CK(cudaStreamSynchronize(h->stream), "init sync");
+    h->pending = 0;
+    if (flags[1]) return fail(h, ESLBM_ERR_NAN, "non-finite initial data");
+    if (flags[0]) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "%llu cells violate the convexity / sub-characteristic condition", flags[0]);
+        return fail(h, ESLBM_ERR_DOMAIN, buf);
+    }
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_init_distributions(eslbm_handle *h, const double *f0, int32_t on_device)
+{
+    if (!h || !f0) return fail(h, ESLBM_ERR_ARG, "null argument");
+    Counters *c = h->counters();
+    CK(cudaMemsetAsync(&c->non_finite, 0, sizeof(unsigned long long), h->stream), "clear flag");
+    const int64_t n = h->sz.ncell;
+    const size_t elem = h->fp64 ? 8 : 4;
+    for (int64_t p = 0; p < h->sz.planes; ++p) {
+        const double *src = f0 + p * n;
+        if (!on_device) {
+            CK(cudaMemcpyAsync(h->spare(), src, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, h->stream),
+               "copy f0");
+            src = (const double *)h->spare();
+        }
+        CK(launch_set(h->fp64, src, (char *)h->f[h->cur] + (size_t)p * (size_t)n * elem, n, c, h->stream), "set");
+    }
+    unsigned long long nf = 0;
+    CK(cudaMemcpyAsync(&nf, &c->non_finite, sizeof(nf), cudaMemcpyDeviceToHost, h->stream), "read flag");
+    CK(cudaStreamSynchronize(h->stream), "sync");
+    h->pending = 0;
+    if (nf) return fail(h, ESLBM_ERR_NAN, "non-finite distributions");
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_step(eslbm_handle *h, int64_t n)
+{
+    if (!h || n < 0) return fail(h, ESLBM_ERR_ARG, "bad step count");
+    while (n > 0) {
+        const bool graph_ok = h->use_graph && h->stream != nullptr;
+        if (graph_ok) {
+            const int gsteps = (h->sz.stages_per_step % 2 == 0) ? 1 : 2;
+            if (n >= gsteps) {
+                if (!h->gexec || h->graph_pending != h->pending || h->graph_cur != h->cur) {
+                    eslbm_status s = capture_graph(h);
+                    if (s != ESLBM_OK) return s;
+                }
+                CK(cudaGraphLaunch(h->gexec, h->stream), "graph launch");
+                h->cur = h->graph_cur_after;
+                h->pending = h->graph_pending_after;
+                h->relaxations += (uint64_t)h->sz.ncell * (uint64_t)(h->sz.stages_per_step * h->graph_steps);
+                n -= h->graph_steps;
+                continue;
+            }
+        }
+        eslbm_status s = run_ops(h);
+        if (s != ESLBM_OK) return s;
+        n -= 1;
+    }
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_transport(eslbm_handle *h, int64_t s)
+{
+    if (!h) return ESLBM_ERR_ARG;
+    h->pending += s;
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_relax(eslbm_handle *h, int32_t kind)
+{
+    if (!h || (kind != ESLBM_RELAX_MAIN && kind != ESLBM_RELAX_PROJECT)) return fail(h, ESLBM_ERR_ARG, "bad kind");
+    eslbm_status s = launch_one_stage(h, h->pending, kind == ESLBM_RELAX_PROJECT ? KIND_PROJECT : KIND_MAIN);
+    if (s == ESLBM_OK) h->pending = 0;
+    return s;
+}
+
+eslbm_status eslbm_read_moments(eslbm_handle *h, double *u_out, int32_t on_device)
+{
+    if (!h || !u_out) return fail(h, ESLBM_ERR_ARG, "null argument");
+    double *dst = on_device ? u_out : (double *)h->spare();
+    CK(launch_gather_moments(h->cfg.dim, h->fp64, h->f[h->cur], dst, h->cfg.nx, h->cfg.ny, (int)h->sz.M,
+                             make_shift(h, h->pending), h->stream),
+       "gather moments");
+    if (!on_device) {
+        CK(cudaMemcpyAsync(u_out, dst, sizeof(double) * (size_t)(h->sz.M * h->sz.ncell), cudaMemcpyDeviceToHost,
+                           h->stream),
+           "copy moments");
+        CK(cudaStreamSynchronize(h->stream), "sync");
+    }
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_read_distributions(eslbm_handle *h, double *f_out, int32_t on_device)
+{
+    if (!h || !f_out) return fail(h, ESLBM_ERR_ARG, "null argument");
+    const Shift sh = make_shift(h, h->pending);
+    const int64_t n = h->sz.ncell;
+    if (on_device) {
+        CK(launch_gather_planes(h->cfg.dim, h->fp64, h->f[h->cur], f_out, h->cfg.nx, h->cfg.ny, (int)h->sz.M, 0,
+                                (int)h->sz.planes, sh, h->stream),
+           "gather planes");
+        return ESLBM_OK;
+    }
+    // through the spare buffer, as many planes at a time as fit
+    const int64_t per = std::max<int64_t>(1, (int64_t)(h->sz.state_bytes / (sizeof(double) * (uint64_t)n)));
+    for (int64_t p = 0; p < h->sz.planes; p += per) {
+        const int np = (int)std::min<int64_t>(per, h->sz.planes - p);
+        CK(launch_gather_planes(h->cfg.dim, h->fp64, h->f[h->cur], (double *)h->spare(), h->cfg.nx, h->cfg.ny,
+                                (int)h->sz.M, (int)p, np, sh, h->stream),
+           "gather planes");
+        CK(cudaMemcpyAsync(f_out + p * n, h->spare(), sizeof(double) * (size_t)(np * n), cudaMemcpyDeviceToHost,
+                           h->stream),
+           "copy planes");
+    }
+    CK(cudaStreamSynchronize(h->stream), "sync");
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_read_totals(eslbm_handle *h, double *out, int32_t on_device)
+{
+    if (!h || !out) return fail(h, ESLBM_ERR_ARG, "null argument");
+    double *dst = on_device ? out : h->totals_out();
+    CK(launch_totals(h->family, h->fp64, h->f[h->cur], h->partials(), dst, h->cfg.nx, h->cfg.ny,
+                     make_shift(h, h->pending), h->P, h->stream),
+       "totals");
+    if (!on_device) {
+        CK(cudaMemcpyAsync(out, dst, sizeof(double) * (size_t)(2 + h->sz.M), cudaMemcpyDeviceToHost, h->stream),
+           "copy totals");
+        CK(cudaStreamSynchronize(h->stream), "sync");
+    }
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_get_diagnostics(eslbm_handle *h, eslbm_diagnostics *out)
+{
+    if (!h || !out) return fail(h, ESLBM_ERR_ARG, "null argument");
+    Counters c;
+    CK(cudaMemcpyAsync(&c, h->counters(), sizeof(c), cudaMemcpyDeviceToHost, h->stream), "read counters");
+    CK(cudaStreamSynchronize(h->stream), "sync");
+    out->relaxations = h->relaxations;
+    out->fallbacks = c.fallbacks;
+    out->entropy_increases = c.entropy_increases;
+    float wmin, wmax;
+    std::memcpy(&wmin, &c.omega_min_bits, sizeof(float));
+    std::memcpy(&wmax, &c.omega_max_bits, sizeof(float));
+    const bool seen = c.omega_min_bits != 0x7f800000u;
+    out->omega_min = seen ? (double)wmin : NAN;
+    out->omega_max = seen ? (double)wmax : NAN;
+    return c.fallbacks ? ESLBM_WARN_OMEGA_FALLBACK : ESLBM_OK;
+}
+
+eslbm_status eslbm_reset_diagnostics(eslbm_handle *h)
+{
+    if (!h) return ESLBM_ERR_ARG;
+    Counters c;
+    std::memset(&c, 0, sizeof(c));
+    c.omega_min_bits = 0x7f800000u;  // +inf
+    c.omega_max_bits = 0u;
+    static_assert(sizeof(Counters) <= kCountersBytes, "counters fit the reserved space");
+    CK(cudaMemcpyAsync(h->counters(), &c, sizeof(c), cudaMemcpyHostToDevice, h->stream), "reset counters");
+    CK(cudaStreamSynchronize(h->stream), "sync");
+    h->relaxations = 0;
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_use_graph(eslbm_handle *h, int32_t enable)
+{
+    if (!h) return ESLBM_ERR_ARG;
+    h->use_graph = enable != 0;
+    if (!h->use_graph && h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    return ESLBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// common.cuh -- shared device-side definitions of the sm_103a composite-step
+// library: launch parameters, velocity sets and small helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace eslbm {
+
+// Physical and numerical parameters of a run, passed by value to kernels.
+struct Params {
+    double V;        // lattice velocity
+    double a[2];     // linear transport velocity
+    double c[2];     // Burgers flux coefficients
+    double g;        // gravity
+    double gamma;    // Euler
+    double omega;    // fixed relaxation parameter
+    double t_max;    // entropic search interval for omega - 1
+};
+
+enum { KIND_MAIN = 0, KIND_PROJECT = 1 };
+
+// Velocity sets of Section 1.2: D1Q2 = (+V, -V); D2Q4 = (+V,0), (0,+V), (-V,0), (0,-V).
+template <int DIM> struct Lattice;
+template <> struct Lattice<1> {
+    static constexpr int Q = 2;
+    __host__ __device__ static constexpr int axis(int) { return 0; }
+    __host__ __device__ static constexpr int sign(int k) { return k == 0 ? 1 : -1; }
+};
+template <> struct Lattice<2> {
+    static constexpr int Q = 4;
+    __host__ __device__ static constexpr int axis(int k) { return k & 1; }
+    __host__ __device__ static constexpr int sign(int k) { return k < 2 ? 1 : -1; }
+};
+
+// Pull offsets of one fused stage: population k at cell x reads the value at
+// x + roff[k] (mod n) along its axis, i.e. x - sign_k * shift (eq. transportPhase).
+struct Shift {
+    int64_t roff[4];
+};
+
+// Device counters (first 64 bytes of the workspace).
+struct Counters {
+    unsigned long long fallbacks;
+    unsigned long long entropy_increases;
+    unsigned int omega_min_bits;   // float bits of the smallest omega (positive floats order as ints)
+    unsigned int omega_max_bits;
+    unsigned long long domain_violations;
+    unsigned long long non_finite;
+    unsigned long long pad[3];
+};
+
+template <class R> struct Tol;
+// Newton stops when its last step is below this fraction of the iterate; one
+// more evaluation then brings the error to the rounding level (quadratic
+// convergence), and the final chord keeps the root on the non-increasing side.
+template <> struct Tol<float> {
+    static constexpr float newton = 1e-4f;
+    static constexpr float inner = 2e-7f;
+    static constexpr float inner_accept = 1e-5f;
+    static constexpr int max_outer = 32;
+    static constexpr int max_inner = 8;
+};
+template <> struct Tol<double> {
+    static constexpr double newton = 1e-9;
+    static constexpr double inner = 4e-16;
+    static constexpr double inner_accept = 1e-12;
+    static constexpr int max_outer = 64;
+    static constexpr int max_inner = 12;
+};
+
+}  // namespace eslbm

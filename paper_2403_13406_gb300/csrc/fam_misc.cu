@@ -1,0 +1,78 @@
+// fam_misc.cu -- Euler (fixed omega), gathers, conversion and the dispatch
+// entry points declared in launch.h.
+#include "family_impl.cuh"
+
+namespace eslbm {
+
+cudaError_t stage_scalar(int, bool, bool, bool, const StageLaunch &);
+cudaError_t stage_sw(int, bool, bool, bool, const StageLaunch &);
+cudaError_t init_scalar(int, bool, const double *, void *, int64_t, const Params &, Counters *, cudaStream_t);
+cudaError_t init_sw(int, bool, const double *, void *, int64_t, const Params &, Counters *, cudaStream_t);
+cudaError_t totals_scalar(int, bool, const void *, double *, double *, int64_t, int64_t, const Shift &,
+                          const Params &, cudaStream_t);
+cudaError_t totals_sw(int, bool, const void *, double *, double *, int64_t, int64_t, const Shift &, const Params &,
+                      cudaStream_t);
+
+cudaError_t launch_stage(int family, bool fp64, bool entropic, bool diag, const StageLaunch &L)
+{
+    if (family == FAM_SW1 || family == FAM_SW2) return stage_sw(family, fp64, entropic, diag, L);
+    if (family == FAM_EULER2) return stage_family<Euler2, 2>(fp64, false, false, L);
+    return stage_scalar(family, fp64, entropic, diag, L);
+}
+
+cudaError_t launch_init_eq(int family, bool fp64, const double *u0, void *f, int64_t ncell, const Params &P,
+                           Counters *cnt, cudaStream_t st)
+{
+    if (family == FAM_SW1 || family == FAM_SW2) return init_sw(family, fp64, u0, f, ncell, P, cnt, st);
+    if (family == FAM_EULER2) return init_family<Euler2>(fp64, u0, f, ncell, P, cnt, st);
+    return init_scalar(family, fp64, u0, f, ncell, P, cnt, st);
+}
+
+cudaError_t launch_totals(int family, bool fp64, const void *f, double *partials, double *out, int64_t nx,
+                          int64_t ny, const Shift &sh, const Params &P, cudaStream_t st)
+{
+    if (family == FAM_SW1 || family == FAM_SW2) return totals_sw(family, fp64, f, partials, out, nx, ny, sh, P, st);
+    if (family == FAM_EULER2) return totals_family<Euler2, 2>(fp64, f, partials, out, nx, ny, sh, P, st);
+    return totals_scalar(family, fp64, f, partials, out, nx, ny, sh, P, st);
+}
+
+template <int DIM, class R, bool MOM>
+static cudaError_t gather_t(const void *f, double *out, int64_t nx, int64_t ny, int M, int p0, int np,
+                            const Shift &sh, cudaStream_t st)
+{
+    dim3 grid((unsigned)((nx + kBlock - 1) / kBlock), (unsigned)ny);
+    k_gather<DIM, R, MOM><<<grid, kBlock, 0, st>>>((const R *)f, out, nx, ny, M, p0, np, sh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_moments(int dim, bool fp64, const void *f, double *out, int64_t nx, int64_t ny, int M,
+                                  const Shift &sh, cudaStream_t st)
+{
+    if (dim == 1)
+        return fp64 ? gather_t<1, double, true>(f, out, nx, ny, M, 0, 0, sh, st)
+                    : gather_t<1, float, true>(f, out, nx, ny, M, 0, 0, sh, st);
+    return fp64 ? gather_t<2, double, true>(f, out, nx, ny, M, 0, 0, sh, st)
+                : gather_t<2, float, true>(f, out, nx, ny, M, 0, 0, sh, st);
+}
+
+cudaError_t launch_gather_planes(int dim, bool fp64, const void *f, double *out, int64_t nx, int64_t ny, int M,
+                                 int plane0, int nplanes, const Shift &sh, cudaStream_t st)
+{
+    if (dim == 1)
+        return fp64 ? gather_t<1, double, false>(f, out, nx, ny, M, plane0, nplanes, sh, st)
+                    : gather_t<1, float, false>(f, out, nx, ny, M, plane0, nplanes, sh, st);
+    return fp64 ? gather_t<2, double, false>(f, out, nx, ny, M, plane0, nplanes, sh, st)
+                : gather_t<2, float, false>(f, out, nx, ny, M, plane0, nplanes, sh, st);
+}
+
+cudaError_t launch_set(bool fp64, const double *src, void *f, int64_t n, Counters *cnt, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)((n + kBlock - 1) / kBlock);
+    if (fp64) k_set<double><<<grid, kBlock, 0, st>>>(src, (double *)f, n, cnt);
+    else k_set<float><<<grid, kBlock, 0, st>>>(src, (float *)f, n, cnt);
+    return cudaGetLastError();
+}
+
+int totals_blocks() { return kRedBlocks; }
+
+}  // namespace eslbm

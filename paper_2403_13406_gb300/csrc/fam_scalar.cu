@@ -1,0 +1,41 @@
+// fam_scalar.cu -- linear transport and Burgers (M = 1), D1Q2 and D2Q4.
+#include "family_impl.cuh"
+
+namespace eslbm {
+
+cudaError_t stage_scalar(int family, bool fp64, bool entropic, bool diag, const StageLaunch &L)
+{
+    switch (family) {
+    case FAM_LINEAR1: return stage_family<Scalar<1, false>, 1>(fp64, entropic, diag, L);
+    case FAM_LINEAR2: return stage_family<Scalar<2, false>, 2>(fp64, entropic, diag, L);
+    case FAM_BURGERS1: return stage_family<Scalar<1, true>, 1>(fp64, entropic, diag, L);
+    case FAM_BURGERS2: return stage_family<Scalar<2, true>, 2>(fp64, entropic, diag, L);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t init_scalar(int family, bool fp64, const double *u0, void *f, int64_t ncell, const Params &P,
+                        Counters *cnt, cudaStream_t st)
+{
+    switch (family) {
+    case FAM_LINEAR1: return init_family<Scalar<1, false>>(fp64, u0, f, ncell, P, cnt, st);
+    case FAM_LINEAR2: return init_family<Scalar<2, false>>(fp64, u0, f, ncell, P, cnt, st);
+    case FAM_BURGERS1: return init_family<Scalar<1, true>>(fp64, u0, f, ncell, P, cnt, st);
+    case FAM_BURGERS2: return init_family<Scalar<2, true>>(fp64, u0, f, ncell, P, cnt, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t totals_scalar(int family, bool fp64, const void *f, double *partials, double *out, int64_t nx,
+                          int64_t ny, const Shift &sh, const Params &P, cudaStream_t st)
+{
+    switch (family) {
+    case FAM_LINEAR1: return totals_family<Scalar<1, false>, 1>(fp64, f, partials, out, nx, ny, sh, P, st);
+    case FAM_LINEAR2: return totals_family<Scalar<2, false>, 2>(fp64, f, partials, out, nx, ny, sh, P, st);
+    case FAM_BURGERS1: return totals_family<Scalar<1, true>, 1>(fp64, f, partials, out, nx, ny, sh, P, st);
+    case FAM_BURGERS2: return totals_family<Scalar<2, true>, 2>(fp64, f, partials, out, nx, ny, sh, P, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace eslbm

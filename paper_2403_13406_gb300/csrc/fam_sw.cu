@@ -1,0 +1,29 @@
+// fam_sw.cu -- shallow water, D1Q2 (M = 2) and D2Q4 (M = 3).
+#include "family_impl.cuh"
+
+namespace eslbm {
+
+cudaError_t stage_sw(int family, bool fp64, bool entropic, bool diag, const StageLaunch &L)
+{
+    if (family == FAM_SW1) return stage_family<ShallowWater<1>, 1>(fp64, entropic, diag, L);
+    if (family == FAM_SW2) return stage_family<ShallowWater<2>, 2>(fp64, entropic, diag, L);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t init_sw(int family, bool fp64, const double *u0, void *f, int64_t ncell, const Params &P,
+                    Counters *cnt, cudaStream_t st)
+{
+    if (family == FAM_SW1) return init_family<ShallowWater<1>>(fp64, u0, f, ncell, P, cnt, st);
+    if (family == FAM_SW2) return init_family<ShallowWater<2>>(fp64, u0, f, ncell, P, cnt, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t totals_sw(int family, bool fp64, const void *f, double *partials, double *out, int64_t nx, int64_t ny,
+                      const Shift &sh, const Params &P, cudaStream_t st)
+{
+    if (family == FAM_SW1) return totals_family<ShallowWater<1>, 1>(fp64, f, partials, out, nx, ny, sh, P, st);
+    if (family == FAM_SW2) return totals_family<ShallowWater<2>, 2>(fp64, f, partials, out, nx, ny, sh, P, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace eslbm

@@ -1,0 +1,276 @@
+// kernels.cuh -- CUDA kernels of the composite step, templated on the system
+// (physics), the dimension and the storage precision.
+//
+// Data layout: structure of arrays, plane (k*M + m) of ncell = nx*ny cells,
+// x fastest.  One thread owns one cell of the output; within a warp the cells
+// are consecutive in x, so every plane access of a warp is one contiguous run
+// of 32 elements (coalesced), also for the shifted pulls.
+#pragma once
+
+#include "systems.cuh"
+
+namespace eslbm {
+
+constexpr int kBlock = 256;       // threads per block of the per-cell kernels
+constexpr int kRedBlocks = 1024;  // fixed grid of the totals reduction (deterministic order)
+constexpr int kRedThreads = 256;
+
+template <class R> struct StageArgs {
+    const R *__restrict__ fin;
+    R *__restrict__ fout;
+    int64_t nx, ny, ncell;
+    Shift sh;
+    int kind;
+    Counters *cnt;
+};
+
+__device__ __forceinline__ int64_t wrap_add(int64_t x, int64_t r, int64_t n)
+{
+    const int64_t s = x + r;
+    return s >= n ? s - n : s;
+}
+
+// source cell of population k for output cell (x, y)
+template <int DIM>
+__device__ __forceinline__ int64_t src_cell(int k, int64_t x, int64_t y, int64_t nx, int64_t ny, const Shift &sh)
+{
+    if (Lattice<DIM>::axis(k) == 0) return y * nx + wrap_add(x, sh.roff[k], nx);
+    return wrap_add(y, sh.roff[k], ny) * nx + x;
+}
+
+__device__ __forceinline__ void warp_count(bool flag, unsigned long long *counter)
+{
+    const unsigned mask = __ballot_sync(0xffffffffu, flag);
+    if (mask && (threadIdx.x & 31) == 0) atomicAdd(counter, (unsigned long long)__popc(mask));
+}
+
+// One relaxation of one cell (eq. relaxationDiscretizationOmega), in place.
+template <class Sys, class R, bool ENTROPIC, bool DIAG>
+__device__ __forceinline__ void relax_cell(const Params &P, R *f, int kind, bool &fallback, bool &increase,
+                                           R &omega_used)
+{
+    constexpr int Q = Sys::Q, M = Sys::M;
+    R u[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        R s = f[m];
+#pragma unroll
+        for (int k = 1; k < Q; ++k) s += f[k * M + m];
+        u[m] = s;
+    }
+    R feq[Q * M];
+    Sys::template equilibrium<R>(P, u, feq);
+    fallback = false;
+    increase = false;
+    if (kind == KIND_PROJECT) {  // R_1: projection on the equilibrium (Section 6.1)
+        omega_used = R(1);
+#pragma unroll
+        for (int i = 0; i < Q * M; ++i) f[i] = feq[i];
+        return;
+    }
+    R delta[Q * M];
+#pragma unroll
+    for (int i = 0; i < Q * M; ++i) delta[i] = feq[i] - f[i];
+    R w = R(P.omega);
+    if constexpr (ENTROPIC && !Sys::LINEAR) {
+        typename Sys::template Ctx<R> cx;
+        Sys::template prepare<R>(P, u, delta, cx);
+        w = entropic_omega<Sys, R>(P, cx, fallback);
+        if constexpr (DIAG) {
+            // per-cell check of Section 4: Sigma(R f) - Sigma(f) = F(omega - 1) <= 0
+            R B1, d1, B0, d0;
+            if (Sys::template eval<R>(P, cx, w - R(1), B1, d1) && Sys::template eval<R>(P, cx, R(-1), B0, d0))
+                increase = (B1 - B0) > R(64) * R(sizeof(R) == 4 ? 1.2e-7 : 2.3e-16) * B0;
+        }
+    } else if constexpr (ENTROPIC) {
+        w = R(2);  // quadratic kinetic entropies: omega* = 2 exactly (Proposition 2)
+    }
+    omega_used = w;
+#pragma unroll
+    for (int i = 0; i < Q * M; ++i) f[i] += w * delta[i];
+}
+
+// Fused stage: pull-shift by sh (transport, eq. transportPhase) then relax.
+template <class Sys, int DIM, class R, bool ENTROPIC, bool DIAG>
+__global__ void __launch_bounds__(kBlock) k_stage(StageArgs<R> a, Params P)
+{
+    constexpr int Q = Sys::Q, M = Sys::M;
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t y = blockIdx.y;
+    const bool valid = x < a.nx;
+    R f[Q * M];
+    bool fb = false, inc = false;
+    R w = R(1);
+    if (valid) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int64_t s = src_cell<DIM>(k, x, y, a.nx, a.ny, a.sh);
+#pragma unroll
+            for (int m = 0; m < M; ++m) f[k * M + m] = a.fin[(int64_t)(k * M + m) * a.ncell + s];
+        }
+        relax_cell<Sys, R, ENTROPIC, DIAG>(P, f, a.kind, fb, inc, w);
+        const int64_t o = y * a.nx + x;
+#pragma unroll
+        for (int i = 0; i < Q * M; ++i) a.fout[(int64_t)i * a.ncell + o] = f[i];
+    }
+    if constexpr (ENTROPIC && !Sys::LINEAR) warp_count(valid && fb, &a.cnt->fallbacks);
+    if constexpr (DIAG) {
+        warp_count(valid && inc, &a.cnt->entropy_increases);
+        float wf = valid ? float(w) : 1.0f;
+        float wmin = wf, wmax = wf;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            wmin = fminf(wmin, __shfl_xor_sync(0xffffffffu, wmin, o));
+            wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&a.cnt->omega_min_bits, __float_as_uint(wmin));
+            atomicMax(&a.cnt->omega_max_bits, __float_as_uint(wmax));
+        }
+    }
+}
+
+// f_k = f^eq_k(u0) (Section 3.1) with the domain check of Section 1.2.
+template <class Sys, class R>
+__global__ void __launch_bounds__(kBlock) k_init_eq(const double *__restrict__ u0, R *__restrict__ f,
+                                                    int64_t ncell, Params P, Counters *cnt)
+{
+    constexpr int Q = Sys::Q, M = Sys::M;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false, nonfinite = false;
+    if (i < ncell) {
+        double u[M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            u[m] = u0[(int64_t)m * ncell + i];
+            nonfinite |= !isfinite(u[m]);
+        }
+        bad = !Sys::template admissible<double>(P, u);
+        double feq[Q * M];
+        Sys::template equilibrium<double>(P, u, feq);
+#pragma unroll
+        for (int j = 0; j < Q * M; ++j) f[(int64_t)j * ncell + i] = R(feq[j]);
+    }
+    warp_count(bad, &cnt->domain_violations);
+    warp_count(nonfinite, &cnt->non_finite);
+}
+
+// distributions from double planes (rounded to the storage precision)
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_set(const double *__restrict__ src, R *__restrict__ f, int64_t n,
+                                                Counters *cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool nonfinite = false;
+    if (i < n) {
+        const double v = src[i];
+        nonfinite = !isfinite(v);
+        f[i] = R(v);
+    }
+    warp_count(nonfinite, &cnt->non_finite);
+}
+
+// Moments u_m = sum_k f_k,m, or the planes [p0, p0 + np) of the logical
+// distributions, as double planes (the pending shift sh is applied).
+template <int DIM, class R, bool MOMENTS>
+__global__ void __launch_bounds__(kBlock) k_gather(const R *__restrict__ f, double *__restrict__ out, int64_t nx,
+                                                   int64_t ny, int M, int p0, int np, Shift sh)
+{
+    constexpr int Q = Lattice<DIM>::Q;
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t y = blockIdx.y;
+    if (x >= nx) return;
+    const int64_t ncell = nx * ny, o = y * nx + x;
+    if (MOMENTS) {
+        for (int m = 0; m < M; ++m) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < Q; ++k)
+                s += double(f[(int64_t)(k * M + m) * ncell + src_cell<DIM>(k, x, y, nx, ny, sh)]);
+            out[(int64_t)m * ncell + o] = s;
+        }
+    } else {
+        for (int p = p0; p < p0 + np; ++p)
+            out[(int64_t)(p - p0) * ncell + o] = double(f[(int64_t)p * ncell + src_cell<DIM>(p / M, x, y, nx, ny, sh)]);
+    }
+}
+
+// Totals (double precision): per cell Sigma(f) = S(u) + sum_k B_k(f_k - f^eq_k),
+// S(u), and u.  Pass 1: fixed grid of kRedBlocks blocks, each reducing a fixed
+// set of cells in a fixed tree order into partials[block][2 + M].
+template <class Sys, int DIM, class R>
+__global__ void __launch_bounds__(kRedThreads) k_totals_partial(const R *__restrict__ f, double *__restrict__ partials,
+                                                                int64_t nx, int64_t ny, Shift sh, Params P)
+{
+    constexpr int Q = Sys::Q, M = Sys::M, NV = 2 + M;
+    const int64_t ncell = nx * ny;
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t y = c / nx, x = c - y * nx;
+        double fc[Q * M], u[M];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int64_t s = src_cell<DIM>(k, x, y, nx, ny, sh);
+#pragma unroll
+            for (int m = 0; m < M; ++m) fc[k * M + m] = double(f[(int64_t)(k * M + m) * ncell + s]);
+        }
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            double s = fc[m];
+#pragma unroll
+            for (int k = 1; k < Q; ++k) s += fc[k * M + m];
+            u[m] = s;
+        }
+        double feq[Q * M], delta[Q * M];
+        Sys::template equilibrium<double>(P, u, feq);
+#pragma unroll
+        for (int i = 0; i < Q * M; ++i) delta[i] = feq[i] - fc[i];
+        const double S = Sys::template entropy<double>(P, u);
+        typename Sys::template Ctx<double> cx;
+        Sys::template prepare<double>(P, u, delta, cx);
+        double E, dE;
+        const bool ok = Sys::template eval<double>(P, cx, -1.0, E, dE);
+        acc[0] += ok ? S + E : NAN;
+        acc[1] += S;
+#pragma unroll
+        for (int m = 0; m < M; ++m) acc[2 + m] += u[m];
+    }
+    __shared__ double sm[NV][kRedThreads];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sm[v][threadIdx.x] = acc[v];
+    __syncthreads();
+    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sm[v][threadIdx.x] += sm[v][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) partials[(int64_t)blockIdx.x * NV + v] = sm[v][0];
+}
+
+// Pass 2: one block sums the partials in a fixed order.
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads) k_totals_final(const double *__restrict__ partials, double *__restrict__ out,
+                                                              int nblocks)
+{
+    constexpr int nv = NV;
+    __shared__ double sm[kRedThreads];
+    for (int v = 0; v < nv; ++v) {
+        double a = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) a += partials[(int64_t)b * nv + v];
+        sm[threadIdx.x] = a;
+        __syncthreads();
+        for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+            if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[v] = sm[0];
+        __syncthreads();
+    }
+}
+
+}  // namespace eslbm

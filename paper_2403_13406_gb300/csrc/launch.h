@@ -1,0 +1,42 @@
+// launch.h -- host-side launchers of the templated kernels, one translation
+// unit per system family so that they compile in parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace eslbm {
+
+struct StageLaunch {
+    const void *fin;
+    void *fout;
+    int64_t nx, ny, ncell;
+    Shift sh;
+    int kind;
+    Counters *cnt;
+    Params P;
+    cudaStream_t stream;
+};
+
+enum Family { FAM_LINEAR1, FAM_LINEAR2, FAM_BURGERS1, FAM_BURGERS2, FAM_SW1, FAM_SW2, FAM_EULER2 };
+
+// fused pull-shift + relaxation stage
+cudaError_t launch_stage(int family, bool fp64, bool entropic, bool diag, const StageLaunch &L);
+// f = f^eq(u0) with the domain check
+cudaError_t launch_init_eq(int family, bool fp64, const double *u0, void *f, int64_t ncell, const Params &P,
+                           Counters *cnt, cudaStream_t st);
+// totals of Sigma, S and u in double precision into out[2 + M]
+cudaError_t launch_totals(int family, bool fp64, const void *f, double *partials, double *out, int64_t nx,
+                          int64_t ny, const Shift &sh, const Params &P, cudaStream_t st);
+// gathers (pending shift applied) and conversion
+cudaError_t launch_gather_moments(int dim, bool fp64, const void *f, double *out, int64_t nx, int64_t ny, int M,
+                                  const Shift &sh, cudaStream_t st);
+cudaError_t launch_gather_planes(int dim, bool fp64, const void *f, double *out, int64_t nx, int64_t ny, int M,
+                                 int plane0, int nplanes, const Shift &sh, cudaStream_t st);
+cudaError_t launch_set(bool fp64, const double *src, void *f, int64_t n, Counters *cnt, cudaStream_t st);
+
+int totals_blocks();
+
+}  // namespace eslbm

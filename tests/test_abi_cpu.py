@@ -1,0 +1,96 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every
+symbol include/eslbm.h declares, and validates configurations."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2403_13406_gb300 import build as cuda_build
+from paper_2403_13406_gb300 import eslbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    cuda_build.build()
+    return eslbm.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "eslbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(eslbm_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(eslbm.EXPORTS)
+
+
+def test_abi_version_and_status_strings(L):
+    assert L.eslbm_abi_version() == 1
+    for s in (0, 1, 2, 3, 4, 5, 100, 77):
+        assert L.eslbm_status_string(s)
+
+
+def q(**kw):
+    base = dict(dim=1, system="burgers", nx=256, V=1.5)
+    base.update(kw)
+    return eslbm.make_config(**base)
+
+
+def test_query_sizes(L):
+    sz = eslbm.query(q(precision="fp32"))
+    assert (sz.q, sz.M, sz.planes, sz.ncell) == (2, 1, 2, 256)
+    assert sz.state_bytes == 2 * 256 * 4
+    assert sz.stages_per_step == 18 and sz.step_cells == 24
+    sz = eslbm.query(q(system="sw", nx=1 << 20, precision="fp64", V=4.0, g=9.81))
+    assert sz.planes == 4 and sz.state_bytes == 4 * (1 << 20) * 8
+    sz = eslbm.query(eslbm.make_config(2, "sw", 100, 50, V=8.0, g=9.81))
+    assert (sz.q, sz.M, sz.ncell) == (4, 3, 5000)
+    sz = eslbm.query(eslbm.make_config(2, "euler", 64, 64, V=6.21))
+    assert sz.planes == 16
+    assert eslbm.query(q(scheme="III")).stages_per_step == 27
+    assert eslbm.query(q(scheme="IV")).stages_per_step == 36
+    assert eslbm.query(q(scheme="plain")).stages_per_step == 1
+    assert eslbm.query(q(scheme="plain")).step_cells == 1
+    assert eslbm.query(q(scheme="B")).step_cells == 4
+
+
+@pytest.mark.parametrize("bad,status", [
+    (dict(dim=3), eslbm.ERR_ARG),
+    (dict(nx=0), eslbm.ERR_ARG),
+    (dict(V=-1.0), eslbm.ERR_ARG),
+    (dict(scheme=9), eslbm.ERR_ARG),
+    (dict(kappa=0), eslbm.ERR_ARG),
+    (dict(system="sw", g=0.0), eslbm.ERR_ARG),
+    (dict(system="linear", a=(1.6, 0.0)), eslbm.ERR_DOMAIN),
+])
+def test_query_rejects(L, bad, status):
+    cfg = q(**bad)
+    with pytest.raises(eslbm.EslbmError) as e:
+        eslbm.query(cfg)
+    assert e.value.status == status
+
+
+def test_entropic_euler_is_unsupported(L):
+    with pytest.raises(eslbm.EslbmError) as e:
+        eslbm.query(eslbm.make_config(2, "euler", 8, 8, V=6.0, omega_mode="entropic"))
+    assert e.value.status == eslbm.ERR_UNSUPPORTED
+
+
+def test_create_rejects_bad_buffers(L):
+    cfg = q()
+    h = ctypes.c_void_p()
+    st = L.eslbm_create(ctypes.byref(cfg), None, None, None, None, ctypes.byref(h))
+    assert st == eslbm.ERR_ARG and not h.value
+    st = L.eslbm_create(ctypes.byref(cfg), 16, 16, 32, None, ctypes.byref(h))  # same buffer twice
+    assert st == eslbm.ERR_ARG
+    st = L.eslbm_create(ctypes.byref(cfg), 17, 48, 64, None, ctypes.byref(h))  # misaligned
+    assert st == eslbm.ERR_ARG
+    assert L.eslbm_destroy(None) == 0

@@ -1,0 +1,333 @@
+"""Parity of the sm_103a composite step (through the C ABI) with the FP64 CPU oracle.
+
+Bars (stated by the benchmark spec for this path): the shift / indexing pass is bit-exact;
+FP64 results agree within 1e-12 relative max-norm; FP32 results within 1e-5
+relative L2.  Sizes span several thread blocks with ragged tails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2403_13406_gb300 import eslbm, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+
+
+def rel_max(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+CASES = {
+    # name: (dim, system, nx, ny, kwargs, initial data)
+    "burgers1d": (1, "burgers", 256, 1, dict(V=1.5), lambda nx, ny: inputs.sine_1d(nx, 0.5, 0.25)),
+    "burgers1d_ragged": (1, "burgers", 1000, 1, dict(V=1.5), lambda nx, ny: inputs.random_scalar_1d(nx, seed=2)),
+    "linear1d": (1, "linear", 777, 1, dict(V=1.0, a=(0.37, 0.0)), lambda nx, ny: inputs.random_scalar_1d(nx, seed=4)),
+    "sw1d": (1, "sw", 1000, 1, dict(V=4.0, g=9.81), lambda nx, ny: inputs.sw_random_1d(nx, seed=3)),
+    "burgers2d": (2, "burgers", 37, 29, dict(V=3.0, c=(1.0, 0.6)),
+                  lambda nx, ny: inputs.burgers_2d(nx, ny, seed=5, noise=1e-3)),
+    "linear2d": (2, "linear", 300, 7, dict(V=1.0, a=(0.2, -0.15)), lambda nx, ny: inputs.linear_sine_2d(nx, ny)),
+    "sw2d": (2, "sw", 33, 27, dict(V=8.0, g=9.81), lambda nx, ny: inputs.sw_random_2d(nx, ny, seed=6)),
+}
+
+
+def oracle_model(dim, system, nx, ny, kw, mode):
+    return O.Model(dim, system, nx, ny, omega_mode=mode, **kw)
+
+
+def gpu_sim(dim, system, nx, ny, kw, mode, precision, scheme="I", **extra):
+    cfg = eslbm.make_config(dim, system, nx, ny, precision=precision, omega_mode=mode, scheme=scheme, **kw, **extra)
+    return eslbm.Simulation(cfg)
+
+
+def run_pair(name, mode, precision, nsteps, scheme="I"):
+    dim, system, nx, ny, kw, init = CASES[name]
+    u0 = init(nx, ny)
+    m = oracle_model(dim, system, nx, ny, kw, mode)
+    f_ref = O.init_equilibrium(m, u0)
+    st = O.Stats()
+    O.composite_steps(m, f_ref, nsteps, scheme=scheme, stats=st)
+    sim = gpu_sim(dim, system, nx, ny, kw, mode, precision, scheme)
+    sim.init_equilibrium(u0)
+    sim.step(nsteps)
+    f = sim.distributions(host=True)
+    diag = sim.diagnostics()
+    sim.close()
+    return f, f_ref, st, diag
+
+
+# ---------------------------------------------------------------------------
+# transport: bit-exact
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("dim,nx,ny", [(1, 1031, 1), (2, 67, 45), (2, 300, 5)])
+def test_transport_is_bit_exact(precision, dim, nx, ny):
+    """T(s) (eq. transportPhase) is a pure permutation: identical to the oracle's unit shifts,
+    through the pending-shift gather and through a fused stage with omega = 0."""
+    system = "sw"
+    kw = dict(V=10.0, g=9.81)
+    m = O.Model(dim, system, nx, ny, **kw)
+    planes = m.q * m.M
+    f0 = inputs.random_distributions(planes, m.grid_shape, seed=11)
+    if precision == "fp32":
+        f0 = f0.astype(np.float32).astype(np.float64)  # exactly representable in the storage
+    for shifts in ([1], [2, -4, 3], [-1, 5, nx + 3, -(2 * nx + 1)]):
+        ref = np.ascontiguousarray(f0.copy())
+        for s in shifts:
+            O.transport(m, ref, s)
+        sim = gpu_sim(dim, system, nx, ny, kw, "fixed", precision)
+        sim.init_distributions(f0)
+        for s in shifts:
+            sim.transport(s)
+        assert np.array_equal(sim.distributions(host=True), ref)
+        sim.close()
+        # the same shifts executed by the stage kernels (relaxation with omega = 0 is the identity)
+        sim = gpu_sim(dim, system, nx, ny, kw, "fixed", precision, omega=0.0)
+        sim.init_distributions(f0)
+        for s in shifts:
+            sim.transport(s)
+            sim.relax()
+        assert np.array_equal(sim.distributions(host=True), ref)
+        sim.close()
+
+
+# ---------------------------------------------------------------------------
+# composite step parity
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("mode", ["fixed", "entropic"])
+def test_composite_fp64(name, mode):
+    f, ref, st, diag = run_pair(name, mode, "fp64", 2)
+    assert rel_max(f, ref) <= FP64_TOL
+    assert diag["fallbacks"] == st.fallbacks == 0
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("mode", ["fixed", "entropic"])
+def test_composite_fp32(name, mode):
+    f, ref, st, diag = run_pair(name, mode, "fp32", 2)
+    assert rel_l2(f, ref) <= FP32_TOL
+    assert diag["fallbacks"] == 0
+
+
+@pytest.mark.parametrize("scheme", ["II", "III", "IV", "plain", "B"])
+@pytest.mark.parametrize("mode", ["fixed", "entropic"])
+def test_scheme_variants_fp64(scheme, mode):
+    f, ref, _, _ = run_pair("burgers1d_ragged", mode, "fp64", 3, scheme=scheme)
+    assert rel_max(f, ref) <= FP64_TOL
+
+
+def test_config1_burgers_n256():
+    """1D Burgers, N = 256, u0 = 0.5 + 0.25 sin(2 pi x), V = 1.5, entropic omega, FP64, to t = 0.1."""
+    N, V = 256, 1.5
+    n = inputs.steps_for(0.1, 1.0 / N, V)
+    f, ref, _, _ = run_pair("burgers1d", "entropic", "fp64", n)
+    assert rel_max(f, ref) <= FP64_TOL
+
+
+# ---------------------------------------------------------------------------
+# readback: moments and totals
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["burgers1d_ragged", "sw1d", "burgers2d", "sw2d", "linear2d"])
+def test_moments_and_totals(name):
+    dim, system, nx, ny, kw, init = CASES[name]
+    u0 = init(nx, ny)
+    m = oracle_model(dim, system, nx, ny, kw, "entropic")
+    ref = O.init_equilibrium(m, u0)
+    O.composite_steps(m, ref, 1)
+    sim = gpu_sim(dim, system, nx, ny, kw, "entropic", "fp64")
+    sim.init_equilibrium(u0)
+    sim.step(1)
+    u = sim.moments(host=True)
+    ud = sim.moments().cpu().numpy()
+    assert np.array_equal(u, ud)
+    assert rel_max(u, O.moments(m, ref)) <= FP64_TOL
+    tot = sim.totals()
+    sig, S = O.entropy_totals(m, ref)
+    assert abs(tot[0] - sig) <= 1e-12 * abs(sig)
+    assert abs(tot[1] - S) <= 1e-12 * abs(S)
+    np.testing.assert_allclose(tot[2:], O.moments(m, ref).reshape(m.M, -1).sum(axis=1), rtol=1e-12, atol=1e-12)
+    sim.close()
+
+
+def test_init_equilibrium_matches_oracle():
+    dim, system, nx, ny, kw, init = CASES["sw2d"]
+    u0 = init(nx, ny)
+    m = oracle_model(dim, system, nx, ny, kw, "fixed")
+    ref = O.init_equilibrium(m, u0)
+    for precision, tol in (("fp64", 1e-15), ("fp32", 6e-8)):
+        sim = gpu_sim(dim, system, nx, ny, kw, "fixed", precision)
+        sim.init_equilibrium(torch.from_numpy(u0).cuda())
+        f = sim.distributions(host=True)
+        assert np.abs(f - ref).max() <= tol * np.abs(ref).max()
+        sim.close()
+
+
+# ---------------------------------------------------------------------------
+# invariants of the GPU path
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_graph_replay_is_identical(precision):
+    dim, system, nx, ny, kw, init = CASES["sw1d"]
+    u0 = init(nx, ny)
+    outs = []
+    for graph in (False, True):
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            sim = gpu_sim(dim, system, nx, ny, kw, "entropic", precision)
+            sim.use_graph(graph)
+            sim.init_equilibrium(u0)
+            sim.step(1)
+            sim.step(4)
+            outs.append(sim.distributions(host=True))
+            sim.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_time_symmetry_entropic_fp64():
+    """eq. symmetryCondition on the GPU: psi(dt) psi(-dt) = Id with the entropic omega."""
+    dim, system, nx, ny, kw, init = CASES["sw1d"]
+    m = oracle_model(dim, system, nx, ny, kw, "entropic")
+    f0 = inputs.perturb(O.init_equilibrium(m, init(nx, ny)), seed=3, scale=1e-4)
+    sim = gpu_sim(dim, system, nx, ny, kw, "entropic", "fp64")
+    sim.init_distributions(f0)
+    for q4 in (1, -1):  # psi(dt/6) = T(1) R T(2) R T(1), then psi(-dt/6)
+        sim.transport(q4)
+        sim.relax()
+        sim.transport(2 * q4)
+        sim.relax()
+        sim.transport(q4)
+    f = sim.distributions(host=True)
+    assert np.abs(f - f0).max() <= 1e-12
+    sim.close()
+
+
+def test_entropy_never_increases_burgers_shock():
+    """Section 5.1 setting (V = 10, 200 points) past the shock: with the entropic omega the
+    total microscopic entropy never increases and no cell increases its entropy."""
+    N, V = 200, 10.0
+    sim = gpu_sim(1, "burgers", N, 1, dict(V=V), "entropic", "fp64", diagnostics=True)
+    sim.init_equilibrium(inputs.sine_1d(N))
+    prev = sim.totals()[0]
+    for _ in range(30):
+        sim.step(1)
+        cur = sim.totals()[0]
+        assert cur <= prev + 1e-12 * abs(prev)
+        prev = cur
+    d = sim.diagnostics()
+    assert d["entropy_increases"] == 0
+    assert d["omega_min"] >= 1.0 and d["omega_max"] <= 4.0
+    sim.close()
+
+
+def test_domain_and_nan_errors():
+    sim = gpu_sim(1, "burgers", 64, 1, dict(V=1.5), "fixed", "fp64")
+    u = np.full((1, 64), 0.5)
+    u[0, 10] = 2.0  # |u| >= V breaks convexity (Example 2)
+    with pytest.raises(eslbm.EslbmError) as e:
+        sim.init_equilibrium(u)
+    assert e.value.status == eslbm.ERR_DOMAIN
+    u[0, 10] = np.nan
+    with pytest.raises(eslbm.EslbmError) as e:
+        sim.init_equilibrium(u)
+    assert e.value.status == eslbm.ERR_NAN
+    sim.close()
+
+
+def test_fallback_is_counted():
+    """No root inside the convexity domain (see the oracle test): omega = 1, counted, warned."""
+    sim = gpu_sim(1, "burgers", 32, 1, dict(V=1.5), "entropic", "fp64")
+    f0 = np.zeros((2, 32))
+    f0[0, :] = 1.5
+    f0[1, :] = -1.5
+    sim.init_distributions(f0)
+    sim.relax()
+    d = sim.diagnostics()
+    assert d["fallbacks"] == 32 and d["status"] == eslbm.WARN_OMEGA_FALLBACK
+    m = O.Model(1, "burgers", 32, V=1.5, omega_mode="entropic")
+    ref = np.ascontiguousarray(f0.copy())
+    O.relax(m, ref)
+    assert rel_max(sim.distributions(host=True), ref) <= FP64_TOL
+    sim.close()
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads: sampled windows against the oracle
+# ---------------------------------------------------------------------------
+
+def window_check(f_in, f_out, m_full, samples, half, kw, mode, tol, dim):
+    """One composite step depends on a cone of half-width sum|shifts| = 36 cells: the oracle
+    runs the step on a periodic window of 2*half+1 cells and its centre must match."""
+    errs = []
+    for pos in samples:
+        if dim == 1:
+            idx = (np.arange(-half, half + 1) + pos) % f_in.shape[-1]
+            win = np.ascontiguousarray(f_in[:, idx])
+            mw = O.Model(1, m_full[0], 2 * half + 1, omega_mode=mode, **kw)
+            O.composite_steps(mw, win, 1)
+            got, ref = f_out[:, pos], win[:, half]
+        else:
+            py, px = pos
+            iy = (np.arange(-half, half + 1) + py) % f_in.shape[-2]
+            ix = (np.arange(-half, half + 1) + px) % f_in.shape[-1]
+            win = np.ascontiguousarray(f_in[:, iy][:, :, ix])
+            mw = O.Model(2, m_full[0], 2 * half + 1, 2 * half + 1, omega_mode=mode, **kw)
+            O.composite_steps(mw, win, 1)
+            got, ref = f_out[:, py, px], win[:, half, half]
+        errs.append(np.abs(got - ref).max() / np.abs(ref).max())
+    assert max(errs) <= tol, errs
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 5e-6)])
+def test_full_size_sw1d_sampled(precision, tol):
+    """1D shallow water at N = 2^20 (g = 9.81, V = 4, entropic), one composite step after a few
+    steps, checked on sampled windows; conserved totals are kept to rounding."""
+    N = 1 << 20
+    kw = dict(V=4.0, g=9.81)
+    sim = gpu_sim(1, "sw", N, 1, kw, "entropic", precision)
+    sim.init_equilibrium(inputs.sw_sine_1d(N, 1.0, 0.1))
+    t0 = sim.totals()
+    sim.step(3)
+    f_in = sim.distributions(host=True)
+    sim.step(1)
+    f_out = sim.distributions(host=True)
+    t1 = sim.totals()
+    rng = np.random.default_rng(1)
+    samples = list(rng.integers(0, N, 6)) + [0, N - 1]
+    window_check(f_in, f_out, ("sw",), samples, 40, kw, "entropic", tol, 1)
+    mass_tol = 1e-13 if precision == "fp64" else 1e-6
+    assert abs(t1[2] - t0[2]) <= mass_tol * abs(t0[2])
+    assert t1[0] <= t0[0] * (1 + (1e-14 if precision == "fp64" else 1e-6))
+    assert sim.diagnostics()["fallbacks"] == 0
+    sim.close()
+
+
+def test_full_size_burgers2d_sampled():
+    """2D Burgers 4096^2 (V = 3, entropic, FP32) one composite step: sampled 81x81 windows."""
+    n = 4096
+    kw = dict(V=3.0)
+    sim = gpu_sim(2, "burgers", n, n, kw, "entropic", "fp32")
+    sim.init_equilibrium(inputs.burgers_2d(n, n, noise=1e-3))
+    sim.step(1)
+    f_in = sim.distributions(host=True)
+    sim.step(1)
+    f_out = sim.distributions(host=True)
+    samples = [(0, 0), (n - 1, 17), (1234, 4000)]
+    window_check(f_in, f_out, ("burgers",), samples, 37, kw, "entropic", 5e-6, 2)
+    sim.close()

@@ -140,7 +140,8 @@ def test_transport_direction():
 
 
 def test_step_lengths():
-    """dt = 24 kappa dx / V for the composite schemes; scheme (B) of Section 6.3 uses 4 dx / V."""
+    """dt = 24 kappa dx / V for the composite schemes; scheme (B) of Section 6.3 uses 4 dx / V and
+    the standard scheme R T one cell."""
     m = O.Model(1, "burgers", 8, V=1.0)
-    assert O.step_length(m, "I") == 24 and O.step_length(m, "plain") == 24
+    assert O.step_length(m, "I") == 24 and O.step_length(m, "plain") == 1
     assert O.step_length(m, "B") == 4

@@ -52,10 +52,8 @@ def plain_burgers_error(N, V=1.2, T=0.1):
     """The standard scheme R T(dx/V) of Section 2.1, run with its own step dt = dx/V."""
     m = O.Model(1, "burgers", N, V=V)
     f = O.init_equilibrium(m, inputs.sine_1d(N))
-    n = n_steps(T, N, V, step=1)
-    for _ in range(n):
-        O.transport(m, f, 1)
-        O.relax(m, f)
+    n = n_steps(T, N, V, step=O.step_length(m, "plain"))
+    O.composite_steps(m, f, n, scheme="plain")
     return l2(O.moments(m, f)[0] - burgers_exact(inputs.grid_1d(N), n * (1.0 / N) / V), 1.0 / N)
 
 
