@@ -59,6 +59,7 @@ template <> struct Tol<float> {
     static constexpr float inner = 2e-7f;
     static constexpr float inner_accept = 1e-5f;
     static constexpr int max_outer = 32;
+    static constexpr int min_inner = 2;
     static constexpr int max_inner = 8;
 };
 template <> struct Tol<double> {
@@ -66,6 +67,7 @@ template <> struct Tol<double> {
     static constexpr double inner = 4e-16;
     static constexpr double inner_accept = 1e-12;
     static constexpr int max_outer = 64;
+    static constexpr int min_inner = 2;
     static constexpr int max_inner = 12;
 };
 

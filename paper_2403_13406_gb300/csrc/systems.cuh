@@ -224,28 +224,35 @@ template <int DIM> struct ShallowWater {
             const R r = hd - vd * h1;
             // linearised guess at b = 0
             const R A0 = W / (R(2) * ck * ck) - R(1);
-            R b = (r - sg * W * h1 / (R(2) * ck)) / (cx.f1[k] * A0);
-            R cp, dW, Wp;
+            const R lin = sg * W * h1 / (R(2) * ck);
+            R b = (r - lin) / (cx.f1[k] * A0);
+            // magnitude of the two terms of the guess: the convergence scale of b, which
+            // itself can be far smaller when they cancel
+            const R bscale = (fabs(r) + fabs(lin)) / (cx.f1[k] * fabs(A0));
+            R cp, dW, Wp, rcp;
             bool conv = false;
             R prev = R(INFINITY);
             for (int it = 0; it < Tol<R>::max_inner; ++it) {
                 cp = ck - sg * b;
                 if (!(cp > R(0))) return false;
-                dW = -(gV4 * h1 + sg * b * W) / cp;
+                rcp = R(1) / cp;
+                dW = -(gV4 * h1 + sg * b * W) * rcp;
                 Wp = W - dW;
                 if (!(Wp > R(0))) return false;
                 const R G = -b * f1p - sg * dW * (W + Wp) * inv16gV - r;
-                const R Gp = f1p * (Wp / (R(2) * cp * cp) - R(1));
+                const R Gp = f1p * (R(0.5) * Wp * rcp * rcp - R(1));
                 if (!(Gp < R(0))) return false;
                 const R db = G / Gp;
                 b -= db;
                 const R ad = fabs(db);
-                if (ad <= Tol<R>::inner * fabs(b)) {
+                // at least min_inner steps for every lane, so that a warp of smooth cells leaves
+                // the loop together
+                if (it + 1 >= Tol<R>::min_inner && ad <= Tol<R>::inner * (fabs(b) + bscale)) {
                     conv = true;
                     break;
                 }
-                if (it >= 2 && ad >= prev) {  // stalled at the rounding level
-                    conv = ad <= Tol<R>::inner_accept * fabs(b);
+                if (it >= Tol<R>::min_inner && ad >= prev) {  // stalled at the rounding level
+                    conv = ad <= Tol<R>::inner_accept * (fabs(b) + bscale);
                     break;
                 }
                 prev = ad;
@@ -321,35 +328,80 @@ struct Euler2 {
 };
 
 // ---------------------------------------------------------------------------
-// Entropic relaxation parameter: safeguarded Newton on the convex, increasing
-// F(t) = sum_k B_k(t delta_k) - E0 over (0, t_max], E0 = sum_k B_k(-delta_k),
-// started at t = 1 (omega = 2, exact for quadratic entropies, Proposition 2).
-// The bracket [lo, hi] keeps F(lo) <= 0 < F(hi) (a point outside the convexity
-// domain counts as above the root).  The result is the chord root of the final
-// bracket, which never exceeds the true root for a convex F: the cell's
-// microscopic entropy does not increase.  No root inside the domain (F stays
-// <= 0 up to t_max or up to the domain edge): fallback to omega = 1.
+// Entropic relaxation parameter: root t* > 0 of the convex, increasing
+// F(t) = B(t) - E0, B(t) = sum_k B_k(t delta_k), E0 = B(-1) (omega = 1 + t).
+//  1. Evaluate B and B' at t = -1 and t = +1 (omega = 2 is exact for quadratic
+//     entropies, Proposition 2, and close to the root for smooth data).
+//  2. B(0) = B'(0) = 0, so these four values fix the quartic model
+//     B(t) ~ b2 t^2 + b3 t^3 + b4 t^4; its root (a few polynomial Newton steps)
+//     is within O(|delta|^3) of t*.
+//  3. Safeguarded Newton on the exact F from there, keeping a bracket
+//     [lo, hi] with F(lo) <= 0 < F(hi) (outside the convexity domain counts as
+//     above the root).  FP32 stops after the first exact evaluation at the
+//     model root (its O(|delta|^3) error is below the storage rounding of
+//     omega delta); FP64 iterates to a relative step of 1e-9 and evaluates once
+//     more.
+//  4. Return the chord root of the final bracket: for a convex F it never
+//     exceeds t*, so the cell's microscopic entropy does not increase.  If
+//     Newton converged from below (every evaluation <= 0 at rounding level),
+//     return lo.  No root inside (0, t_max] or inside the convexity domain:
+//     fallback omega = 1 (projection).
 // ---------------------------------------------------------------------------
 
 template <class Sys, class R>
 __device__ R entropic_omega(const Params &P, const typename Sys::template Ctx<R> &cx, bool &fallback)
 {
     fallback = false;
-    R E0, dE0;
-    if (!Sys::template eval<R>(P, cx, R(-1), E0, dE0)) {
+    R Em, dEm;
+    if (!Sys::template eval<R>(P, cx, R(-1), Em, dEm)) {
         fallback = true;
         return R(1);
     }
-    if (!(E0 > R(0))) return R(2);  // at equilibrium (to rounding): every omega is the identity
+    if (!(Em > R(0))) return R(2);  // at equilibrium (to rounding): every omega is the identity
     R lo = R(0), hi = R(P.t_max);
-    R Flo = -E0, Fhi = R(0);
+    R Flo = -Em, Fhi = R(0);
     bool hi_ok = false;
-    R t = R(1) < hi ? R(1) : R(0.5) * hi;
-    bool last = false;
+    R t;
+    bool last = false, last_newton = false;
+    R Bp, dBp;
+    if (R(1) < hi && Sys::template eval<R>(P, cx, R(1), Bp, dBp)) {
+        const R F1 = Bp - Em;
+        if (F1 == R(0)) return R(2);
+        if (F1 < R(0)) {
+            lo = R(1);
+            Flo = F1;
+        } else {
+            hi = R(1);
+            Fhi = F1;
+            hi_ok = true;
+        }
+        // quartic model through B(0) = B'(0) = 0 and B, B' at t = -1, +1
+        const R b3 = R(0.5) * (Bp - Em);
+        const R b4 = R(0.25) * ((dBp - dEm) - R(2) * (Bp + Em));
+        const R b2 = R(0.5) * (Bp + Em) - b4;
+        R tm = R(1);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const R m = tm * tm * (b2 + tm * (b3 + tm * b4)) - Em;
+            const R dm = tm * (R(2) * b2 + tm * (R(3) * b3 + R(4) * b4 * tm));
+            tm -= m / dm;
+        }
+        if (tm > lo && tm < hi) {
+            t = tm;
+            last = sizeof(R) == 4;  // FP32: one exact evaluation at the model root
+            last_newton = true;
+        } else {
+            const R tn = R(1) - F1 / dBp;
+            t = (dBp > R(0) && tn > lo && tn < hi) ? tn : R(0.5) * (lo + hi);
+        }
+    } else {
+        hi = R(1) < hi ? R(1) : hi;  // t = 1 leaves the convexity domain (or exceeds t_max)
+        t = R(0.5) * hi;
+    }
     for (int it = 0; it < Tol<R>::max_outer; ++it) {
         R F, dF;
         const bool ok = Sys::template eval<R>(P, cx, t, F, dF);
-        if (ok) F -= E0;
+        if (ok) F -= Em;
         if (ok && F <= R(0)) {
             lo = t;
             Flo = F;
@@ -359,13 +411,23 @@ __device__ R entropic_omega(const Params &P, const typename Sys::template Ctx<R>
             hi_ok = ok;
         }
         if (last || (ok && F == R(0))) break;
-        R tn = (ok && dF > R(0)) ? t - F / dF : R(-1);
-        if (!(tn > lo && tn < hi)) tn = R(0.5) * (lo + hi);
-        if (fabs(tn - t) <= Tol<R>::newton * tn) last = true;
+        bool newton = ok && dF > R(0);
+        R tn = newton ? t - F / dF : R(-1);
+        if (!(tn > lo && tn < hi)) {
+            tn = R(0.5) * (lo + hi);
+            newton = false;
+        }
+        if (fabs(tn - t) <= Tol<R>::newton * tn) {
+            last = true;
+            last_newton = newton;
+        }
         t = tn;
     }
     if (Flo == R(0) && lo > R(0)) return R(1) + lo;
     if (!hi_ok) {
+        // Newton converged from below (every evaluation <= 0 within rounding): lo is the root;
+        // otherwise the bracket collapsed on t_max or on the domain edge: no root
+        if (last && last_newton) return R(1) + lo;
         fallback = true;
         return R(1);
     }
