@@ -111,6 +111,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def aggregate(total_ms, units_per_rank, dist=None, device=None):
+    """Whole-job throughput: every rank times its own replica; the job time is the maximum over
+    ranks and the value counts the units of all ranks.  Returns (value, max_ms)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * units_per_rank / (total_ms * 1e-3), total_ms
+
+
 # ---------------------------------------------------------------------------
 # reference arm / CPU baseline: the FP64 oracle on a bounded sample
 # ---------------------------------------------------------------------------
@@ -220,12 +233,7 @@ def main():
             dist.barrier()
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
     stage_ms = [e[1].elapsed_time(e[2]) / stages for e in evs]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * N * n_steps * args.steps / (total_ms * 1e-3)
+    value, total_ms = aggregate(sum(step_ms), N * n_steps * args.steps, dist, dev)
 
     # dominant kernel: the fused stage (moves every distribution in and out once)
     bytes_per_stage = 2 * int(sim.sizes.planes) * N * 4

@@ -14,8 +14,8 @@ import numpy as np
 
 from . import build as _build
 
-LINEAR, BURGERS, SW = 0, 1, 2
-SYSTEMS = {"linear": LINEAR, "burgers": BURGERS, "sw": SW, "shallow_water": SW}
+LINEAR, BURGERS, SW, EULER = 0, 1, 2, 3
+SYSTEMS = {"linear": LINEAR, "burgers": BURGERS, "sw": SW, "shallow_water": SW, "euler": EULER}
 FIXED, ENTROPIC = 0, 1
 R_MAIN, R_PROJECT = 0, 1
 SCHEMES = {"I": 1, "II": 2, "III": 3, "IV": 4, "plain": 5, "B": 6}
@@ -27,7 +27,7 @@ class _Model(ctypes.Structure):
                 ("kappa", ctypes.c_int), ("V", ctypes.c_double),
                 ("a", ctypes.c_double * 2), ("c", ctypes.c_double * 2),
                 ("g", ctypes.c_double), ("omega_mode", ctypes.c_int),
-                ("omega", ctypes.c_double), ("t_max", ctypes.c_double)]
+                ("omega", ctypes.c_double), ("t_max", ctypes.c_double), ("gamma", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -100,7 +100,7 @@ class Model:
     """
 
     def __init__(self, dim, system, nx, ny=1, V=1.0, a=(0.0, 0.0), c=(1.0, 1.0), g=1.0,
-                 omega_mode="fixed", omega=2.0, t_max=3.0, kappa=1):
+                 omega_mode="fixed", omega=2.0, t_max=3.0, kappa=1, gamma=1.4):
         self.dim = int(dim)
         self.system = SYSTEMS[system] if isinstance(system, str) else int(system)
         self.nx, self.ny = int(nx), (int(ny) if dim == 2 else 1)
@@ -108,7 +108,7 @@ class Model:
         self.c_struct = _Model(self.dim, self.system, self.nx, self.ny, int(kappa), self.V,
                                (ctypes.c_double * 2)(*a), (ctypes.c_double * 2)(*c), float(g),
                                ENTROPIC if omega_mode == "entropic" else FIXED,
-                               float(omega), float(t_max))
+                               float(omega), float(t_max), float(gamma))
         if lib().or_check(ctypes.byref(self.c_struct)) != 0:
             raise ValueError("invalid oracle model")
         self.q = lib().or_q(ctypes.byref(self.c_struct))
@@ -131,7 +131,7 @@ class Model:
         base = dict(dim=self.dim, system=self.system, nx=self.nx, ny=self.ny, V=s.V,
                     a=tuple(s.a), c=tuple(s.c), g=s.g,
                     omega_mode="entropic" if s.omega_mode == ENTROPIC else "fixed",
-                    omega=s.omega, t_max=s.t_max, kappa=s.kappa)
+                    omega=s.omega, t_max=s.t_max, kappa=s.kappa, gamma=s.gamma)
         base.update(kw)
         return Model(**base)
 
@@ -148,27 +148,27 @@ def _check_f(m, f):
 # ---- per-cell quantities ---------------------------------------------------
 
 def flux(m, j, u):
-    u = _vec(u, 3)
-    out = np.zeros(3)
+    u = _vec(u, 4)
+    out = np.zeros(4)
     lib().or_flux(m.ref, j, _ptr(u), _ptr(out))
     return out[: m.M]
 
 
 def dual(m, u):
-    u = _vec(u, 3)
-    p = np.zeros(3)
+    u = _vec(u, 4)
+    p = np.zeros(4)
     lib().or_dual(m.ref, _ptr(u), _ptr(p))
     return p[: m.M]
 
 
 def entropy_S(m, u):
-    return lib().or_entropy_S(m.ref, _ptr(_vec(u, 3)))
+    return lib().or_entropy_S(m.ref, _ptr(_vec(u, 4)))
 
 
 def equilibrium(m, u):
     """f^eq_k(u) for one cell, shape (q, M)."""
-    out = np.zeros(12)
-    lib().or_equilibrium(m.ref, _ptr(_vec(u, 3)), _ptr(out))
+    out = np.zeros(16)
+    lib().or_equilibrium(m.ref, _ptr(_vec(u, 4)), _ptr(out))
     return out[: m.q * m.M].reshape(m.q, m.M)
 
 

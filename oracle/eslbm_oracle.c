@@ -36,7 +36,11 @@
 
 int or_q(const or_model *m) { return m->dim == 1 ? 2 : 4; }
 
-int or_M(const or_model *m) { return m->system == OR_SW ? m->dim + 1 : 1; }
+int or_M(const or_model *m)
+{
+    if (m->system == OR_EULER) return 4;
+    return m->system == OR_SW ? m->dim + 1 : 1;
+}
 
 long or_ncell(const or_model *m) { return m->nx * (m->dim == 1 ? 1 : m->ny); }
 
@@ -52,7 +56,9 @@ int or_check(const or_model *m)
 {
     if (!m) return -1;
     if (m->dim != 1 && m->dim != 2) return -1;
-    if (m->system < OR_LINEAR || m->system > OR_SW) return -1;
+    if (m->system < OR_LINEAR || m->system > OR_EULER) return -1;
+    if (m->system == OR_EULER && (m->dim != 2 || !(m->gamma > 1.0) || m->omega_mode != OR_OMEGA_FIXED))
+        return -1;
     if (m->nx < 1 || (m->dim == 2 && m->ny < 1)) return -1;
     if (m->kappa < 1) return -1;
     if (!(m->V > 0.0)) return -1;
@@ -76,6 +82,16 @@ void or_flux(const or_model *m, int j, const double *u, double *phi)
     case OR_BURGERS:
         phi[0] = m->c[j] * 0.5 * u[0] * u[0];
         break;
+    case OR_EULER: { /* (rho, rho u, rho v, E), p = (gamma - 1)(E - rho |v|^2 / 2) (Section 6.3) */
+        double rho = u[0], vx = u[1] / rho, vy = u[2] / rho, E = u[3];
+        double p = (m->gamma - 1.0) * (E - 0.5 * rho * (vx * vx + vy * vy));
+        double v = j == 0 ? vx : vy;
+        phi[0] = rho * v;
+        phi[1] = u[1] * v + (j == 0 ? p : 0.0);
+        phi[2] = u[2] * v + (j == 1 ? p : 0.0);
+        phi[3] = v * (E + p);
+        break;
+    }
     default: { /* shallow water (h, hu[, hv]) */
         double h = u[0];
         if (m->dim == 1) {
@@ -98,6 +114,7 @@ void or_flux(const or_model *m, int j, const double *u, double *phi)
    (shallow water, Example 3) */
 double or_entropy_S(const or_model *m, const double *u)
 {
+    if (m->system == OR_EULER) return NAN; /* no kinetic entropies for Euler in the paper */
     if (m->system != OR_SW) return 0.5 * u[0] * u[0];
     double h = u[0], ke = 0.0;
     for (int i = 1; i <= m->dim; ++i) ke += u[i] * u[i];
@@ -107,6 +124,10 @@ double or_entropy_S(const or_model *m, const double *u)
 /* p = grad S(u); shallow water: p = (g h - |v|^2/2, v) (Example 3) */
 void or_dual(const or_model *m, const double *u, double *p)
 {
+    if (m->system == OR_EULER) {
+        for (int i = 0; i < 4; ++i) p[i] = NAN;
+        return;
+    }
     if (m->system != OR_SW) {
         p[0] = u[0];
         return;
@@ -124,7 +145,7 @@ void or_dual(const or_model *m, const double *u, double *p)
 void or_equilibrium(const or_model *m, const double *u, double *feq)
 {
     int q = or_q(m), M = or_M(m);
-    double phi[2][4];
+    double phi[2][4] = {{0}};
     or_flux(m, 0, u, phi[0]);
     if (m->dim == 2) or_flux(m, 1, u, phi[1]);
     for (int k = 0; k < q; ++k) {
@@ -189,6 +210,13 @@ static void dual_pair(const or_model *m, int j, const double *p, double *Ss, dou
 double or_kinetic_dual(const or_model *m, int k, const double *p, double *grad, double *hess)
 {
     int M = or_M(m), q = or_q(m);
+    if (m->system == OR_EULER) {
+        for (int i = 0; i < M; ++i) {
+            if (grad) grad[i] = NAN;
+            for (int l = 0; l < M && hess; ++l) hess[i * M + l] = NAN;
+        }
+        return NAN;
+    }
     int j = vel_axis(m, k);
     double sg = (double)vel_sign(m, k) / (2.0 * m->V);
     double Ss, Gs, gS[3], gG[3], hS[9], hG[9];
@@ -416,15 +444,15 @@ double or_kinetic_entropy(const or_model *m, int k, const double *fk, const doub
 
 typedef struct {
     const or_model *m;
-    double u[3];
-    double delta[4 * 3]; /* delta_k = f^eq_k - f_k */
+    double u[4];
+    double delta[4 * 4]; /* delta_k = f^eq_k - f_k */
     double E0;           /* sum_k B_k(-delta_k) = Sigma(f) - S(u) */
 } imbalance_ctx;
 
 static int prepare(const or_model *m, const double *fcell, imbalance_ctx *c)
 {
     int q = or_q(m), M = or_M(m);
-    double feq[12];
+    double feq[16];
     c->m = m;
     for (int i = 0; i < M; ++i) {
         double s = 0.0;
@@ -516,7 +544,7 @@ void or_init_equilibrium(const or_model *m, const double *u0, double *f)
 {
     int q = or_q(m), M = or_M(m);
     long n = or_ncell(m);
-    double u[3], feq[12];
+    double u[4], feq[16];
     for (long x = 0; x < n; ++x) {
         for (int i = 0; i < M; ++i) u[i] = u0[(long)i * n + x];
         or_equilibrium(m, u, feq);
@@ -561,7 +589,7 @@ int or_relax(const or_model *m, double *f, int kind, or_stats *st)
 {
     int q = or_q(m), M = or_M(m);
     long n = or_ncell(m);
-    double fc[12], u[3], feq[12];
+    double fc[16], u[4], feq[16];
     for (long x = 0; x < n; ++x) {
         for (int l = 0; l < q * M; ++l) fc[l] = f[(long)l * n + x];
         double w;
@@ -687,6 +715,11 @@ void or_moments(const or_model *m, const double *f, double *u)
 void or_entropy_totals(const or_model *m, const double *f, double *sigma_total, double *S_total)
 {
     int q = or_q(m), M = or_M(m);
+    if (m->system == OR_EULER) {
+        *sigma_total = NAN;
+        *S_total = NAN;
+        return;
+    }
     long n = or_ncell(m);
     double sig = 0.0, S = 0.0, u[3], p[3], fk[3];
     for (long x = 0; x < n; ++x) {

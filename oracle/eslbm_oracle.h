@@ -27,7 +27,7 @@
 extern "C" {
 #endif
 
-enum { OR_LINEAR = 0, OR_BURGERS = 1, OR_SW = 2 };
+enum { OR_LINEAR = 0, OR_BURGERS = 1, OR_SW = 2, OR_EULER = 3 };
 enum { OR_OMEGA_FIXED = 0, OR_OMEGA_ENTROPIC = 1 };
 /* which relaxation a stage applies: the scheme's main one (fixed omega or
    entropic omega), or the projection on the equilibrium R_1 (Section 6.1) */
@@ -51,6 +51,7 @@ typedef struct {
     int omega_mode;   /* OR_OMEGA_FIXED or OR_OMEGA_ENTROPIC */
     double omega;     /* relaxation parameter in fixed mode */
     double t_max;     /* entropic mode: search omega - 1 in [0, t_max] */
+    double gamma;     /* Euler: ratio of specific heats (fixed omega only; no kinetic entropy) */
 } or_model;
 
 typedef struct {

@@ -249,6 +249,67 @@ eslbm_status run_ops(eslbm_handle *h)
     return ESLBM_OK;
 }
 
+// 1D runs without per-cell diagnostics use the temporally blocked kernel: the
+// stages of `steps` consecutive steps (merged shifts, as in run_ops) in one launch.
+bool fused_path(const eslbm_handle *h) { return h->cfg.dim == 1 && h->cfg.diagnostics == 0; }
+
+// steps fused into one launch: one composite step, or up to 24 steps of the short schemes
+int64_t fused_group(const eslbm_handle *h)
+{
+    const int64_t sps = h->sz.stages_per_step;
+    return sps >= 16 ? 1 : std::max<int64_t>(1, 24 / sps);
+}
+
+eslbm_status run_fused(eslbm_handle *h, int64_t steps)
+{
+    FusedLaunch L;
+    L.sl.n = 0;
+    L.sl.halo = 0;
+    for (int64_t i = 0; i < steps; ++i) {
+        for (const Op &op : h->ops) {
+            if (!op.relax) {
+                h->pending += op.shift;
+                continue;
+            }
+            if (L.sl.n >= kMaxFusedStages) return fail(h, ESLBM_ERR_ARG, "too many fused stages");
+            const int64_t s = h->pending;
+            if (s > (1 << 20) || s < -(1 << 20)) return fail(h, ESLBM_ERR_ARG, "shift too large to fuse");
+            L.sl.shift[L.sl.n] = (int)s;
+            L.sl.kind[L.sl.n] = op.kind;
+            L.sl.halo += (int)(s < 0 ? -s : s);
+            L.sl.n += 1;
+            h->pending = 0;
+        }
+    }
+    if (L.sl.n == 0) return ESLBM_OK;
+    L.fin = h->f[h->cur];
+    L.fout = h->f[1 - h->cur];
+    L.n = h->cfg.nx;
+    L.cnt = h->counters();
+    L.P = h->P;
+    L.stream = h->stream;
+    CK(launch_fused1d(h->family, h->fp64, h->cfg.omega_mode == ESLBM_OMEGA_ENTROPIC, L), "fused step launch");
+    h->cur = 1 - h->cur;
+    h->relaxations += (uint64_t)h->sz.ncell * (uint64_t)L.sl.n;
+    return ESLBM_OK;
+}
+
+// one unit of eslbm_step: a fused group of steps, or one step of per-stage launches
+int64_t unit_steps(const eslbm_handle *h) { return fused_path(h) ? fused_group(h) : 1; }
+
+eslbm_status run_unit(eslbm_handle *h, int64_t steps)
+{
+    if (fused_path(h)) return run_fused(h, steps);
+    for (int64_t i = 0; i < steps; ++i) {
+        eslbm_status s = run_ops(h);
+        if (s != ESLBM_OK) return s;
+    }
+    return ESLBM_OK;
+}
+
+// buffer swaps per unit (the graph must return the ping-pong buffers to their start)
+int64_t unit_swaps(const eslbm_handle *h) { return fused_path(h) ? 1 : h->sz.stages_per_step; }
+
 eslbm_status capture_graph(eslbm_handle *h)
 {
     if (h->gexec) {
@@ -258,10 +319,11 @@ eslbm_status capture_graph(eslbm_handle *h)
     const int64_t pend0 = h->pending;
     const int cur0 = h->cur;
     const uint64_t rel0 = h->relaxations;
-    const int nsteps = (h->sz.stages_per_step % 2 == 0) ? 1 : 2;
+    const int units = (unit_swaps(h) % 2 == 0) ? 1 : 2;
+    const int nsteps = units * (int)unit_steps(h);
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     eslbm_status s = ESLBM_OK;
-    for (int i = 0; i < nsteps && s == ESLBM_OK; ++i) s = run_ops(h);
+    for (int i = 0; i < units && s == ESLBM_OK; ++i) s = run_unit(h, unit_steps(h));
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     h->graph_cur_after = h->cur;
@@ -442,7 +504,7 @@ eslbm_status eslbm_step(eslbm_handle *h, int64_t n)
     while (n > 0) {
         const bool graph_ok = h->use_graph && h->stream != nullptr;
         if (graph_ok) {
-            const int gsteps = (h->sz.stages_per_step % 2 == 0) ? 1 : 2;
+            const int64_t gsteps = ((unit_swaps(h) % 2 == 0) ? 1 : 2) * unit_steps(h);
             if (n >= gsteps) {
                 if (!h->gexec || h->graph_pending != h->pending || h->graph_cur != h->cur) {
                     eslbm_status s = capture_graph(h);
@@ -456,9 +518,10 @@ eslbm_status eslbm_step(eslbm_handle *h, int64_t n)
                 continue;
             }
         }
-        eslbm_status s = run_ops(h);
+        const int64_t k = std::min<int64_t>(n, unit_steps(h));
+        eslbm_status s = run_unit(h, k);
         if (s != ESLBM_OK) return s;
-        n -= 1;
+        n -= k;
     }
     return ESLBM_OK;
 }

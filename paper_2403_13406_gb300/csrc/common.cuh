@@ -18,6 +18,32 @@ struct Params {
     double t_max;    // entropic search interval for omega - 1
 };
 
+// The same parameters in the arithmetic type of a kernel (converted once on the
+// host, so a float kernel executes no double-precision instruction), with the
+// derived constants the kernels need.
+template <class R> struct ParamsR {
+    R V, inv2V, a[2], c[2], g, gamma_m1, omega, t_max;
+    R gV4, inv16gV;  // 4 g V and 1 / (16 g V) (shallow water)
+};
+
+template <class R> inline ParamsR<R> params_as(const Params &P)
+{
+    ParamsR<R> q;
+    q.V = R(P.V);
+    q.inv2V = R(0.5 / P.V);
+    q.a[0] = R(P.a[0]);
+    q.a[1] = R(P.a[1]);
+    q.c[0] = R(P.c[0]);
+    q.c[1] = R(P.c[1]);
+    q.g = R(P.g);
+    q.gamma_m1 = R(P.gamma - 1.0);
+    q.omega = R(P.omega);
+    q.t_max = R(P.t_max);
+    q.gV4 = R(4.0 * P.g * P.V);
+    q.inv16gV = P.g > 0 ? R(1.0 / (16.0 * P.g * P.V)) : R(0);
+    return q;
+}
+
 enum { KIND_MAIN = 0, KIND_PROJECT = 1 };
 
 // Velocity sets of Section 1.2: D1Q2 = (+V, -V); D2Q4 = (+V,0), (0,+V), (-V,0), (0,-V).
@@ -39,6 +65,15 @@ struct Shift {
     int64_t roff[4];
 };
 
+// Stages fused into one launch of the temporally blocked 1D kernel.
+constexpr int kMaxFusedStages = 64;
+struct StageList {
+    int n;                       // stages
+    int halo;                    // sum of |shift|
+    int shift[kMaxFusedStages];  // transport before each relaxation
+    int kind[kMaxFusedStages];   // KIND_MAIN or KIND_PROJECT
+};
+
 // Device counters (first 64 bytes of the workspace).
 struct Counters {
     unsigned long long fallbacks;
@@ -56,8 +91,8 @@ template <class R> struct Tol;
 // convergence), and the final chord keeps the root on the non-increasing side.
 template <> struct Tol<float> {
     static constexpr float newton = 1e-4f;
-    static constexpr float inner = 2e-7f;
-    static constexpr float inner_accept = 1e-5f;
+    static constexpr float inner = 2e-6f;
+    static constexpr float inner_accept = 1e-4f;
     static constexpr int max_outer = 32;
     static constexpr int min_inner = 2;
     static constexpr int max_inner = 8;

@@ -13,6 +13,16 @@ cudaError_t totals_scalar(int, bool, const void *, double *, double *, int64_t, 
 cudaError_t totals_sw(int, bool, const void *, double *, double *, int64_t, int64_t, const Shift &, const Params &,
                       cudaStream_t);
 
+cudaError_t fused_scalar(int, bool, bool, const FusedLaunch &);
+cudaError_t fused_sw(int, bool, bool, const FusedLaunch &);
+
+cudaError_t launch_fused1d(int family, bool fp64, bool entropic, const FusedLaunch &L)
+{
+    if (family == FAM_SW1) return fused_sw(family, fp64, entropic, L);
+    if (family == FAM_LINEAR1 || family == FAM_BURGERS1) return fused_scalar(family, fp64, entropic, L);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_stage(int family, bool fp64, bool entropic, bool diag, const StageLaunch &L)
 {
     if (family == FAM_SW1 || family == FAM_SW2) return stage_sw(family, fp64, entropic, diag, L);

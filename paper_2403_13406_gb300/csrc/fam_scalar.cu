@@ -14,6 +14,13 @@ cudaError_t stage_scalar(int family, bool fp64, bool entropic, bool diag, const 
     return cudaErrorInvalidValue;
 }
 
+cudaError_t fused_scalar(int family, bool fp64, bool entropic, const FusedLaunch &L)
+{
+    if (family == FAM_LINEAR1) return fused_family<Scalar<1, false>>(fp64, entropic, L);
+    if (family == FAM_BURGERS1) return fused_family<Scalar<1, true>>(fp64, entropic, L);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t init_scalar(int family, bool fp64, const double *u0, void *f, int64_t ncell, const Params &P,
                         Counters *cnt, cudaStream_t st)
 {

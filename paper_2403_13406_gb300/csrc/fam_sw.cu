@@ -10,6 +10,12 @@ cudaError_t stage_sw(int family, bool fp64, bool entropic, bool diag, const Stag
     return cudaErrorInvalidValue;
 }
 
+cudaError_t fused_sw(int family, bool fp64, bool entropic, const FusedLaunch &L)
+{
+    if (family == FAM_SW1) return fused_family<ShallowWater<1>>(fp64, entropic, L);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t init_sw(int family, bool fp64, const double *u0, void *f, int64_t ncell, const Params &P,
                     Counters *cnt, cudaStream_t st)
 {

@@ -11,7 +11,7 @@ cudaError_t stage_one(const StageLaunch &L)
 {
     StageArgs<R> a{(const R *)L.fin, (R *)L.fout, L.nx, L.ny, L.ncell, L.sh, L.kind, L.cnt};
     dim3 grid((unsigned)((L.nx + kBlock - 1) / kBlock), (unsigned)L.ny);
-    k_stage<Sys, DIM, R, ENT, DIAG><<<grid, kBlock, 0, L.stream>>>(a, L.P);
+    k_stage<Sys, DIM, R, ENT, DIAG><<<grid, kBlock, 0, L.stream>>>(a, params_as<R>(L.P));
     return cudaGetLastError();
 }
 
@@ -35,13 +35,64 @@ cudaError_t stage_family(bool fp64, bool entropic, bool diag, const StageLaunch 
     return fp64 ? stage_prec<Sys, DIM, double>(entropic, diag, L) : stage_prec<Sys, DIM, float>(entropic, diag, L);
 }
 
+// Tile of the fused 1D kernel: about four resident blocks per SM over the grid
+// (a multiple of 32 cells), at least 128 cells, and a window that fits 96 KiB of
+// shared memory.
+inline int fused_tile(int64_t n, int halo, int bytes_per_cell)
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    int64_t t = (n + 4 * sms - 1) / (4 * sms);
+    t = ((t + 31) / 32) * 32;
+    if (t < 128) t = 128;
+    const int64_t tmax = (96 * 1024) / bytes_per_cell - 2 * halo;
+    if (t > tmax) t = tmax;
+    return (int)t;
+}
+
+template <class Sys, class R, bool ENT>
+cudaError_t fused_one(const FusedLaunch &L)
+{
+    constexpr int NP = Sys::Q * Sys::M;
+    const int tile = fused_tile(L.n, L.sl.halo, NP * (int)sizeof(R));
+    if (tile < 32) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(tile + 2 * L.sl.halo) * NP * sizeof(R);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_step1d<Sys, R, ENT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024 + 64);
+        attr_set = true;
+    }
+    FusedArgs<R> a{(const R *)L.fin, (R *)L.fout, L.n, tile, L.cnt};
+    const unsigned grid = (unsigned)((L.n + tile - 1) / tile);
+    k_step1d<Sys, R, ENT><<<grid, kBlock, smem, L.stream>>>(a, L.sl, params_as<R>(L.P));
+    return cudaGetLastError();
+}
+
+template <class Sys>
+cudaError_t fused_family(bool fp64, bool entropic, const FusedLaunch &L)
+{
+    if constexpr (Sys::LINEAR) {
+        (void)entropic;
+        return fp64 ? fused_one<Sys, double, false>(L) : fused_one<Sys, float, false>(L);
+    } else {
+        if (fp64) return entropic ? fused_one<Sys, double, true>(L) : fused_one<Sys, double, false>(L);
+        return entropic ? fused_one<Sys, float, true>(L) : fused_one<Sys, float, false>(L);
+    }
+}
+
 template <class Sys>
 cudaError_t init_family(bool fp64, const double *u0, void *f, int64_t ncell, const Params &P, Counters *cnt,
                         cudaStream_t st)
 {
     const unsigned grid = (unsigned)((ncell + kBlock - 1) / kBlock);
-    if (fp64) k_init_eq<Sys, double><<<grid, kBlock, 0, st>>>(u0, (double *)f, ncell, P, cnt);
-    else k_init_eq<Sys, float><<<grid, kBlock, 0, st>>>(u0, (float *)f, ncell, P, cnt);
+    const ParamsR<double> Pd = params_as<double>(P);
+    if (fp64) k_init_eq<Sys, double><<<grid, kBlock, 0, st>>>(u0, (double *)f, ncell, Pd, cnt);
+    else k_init_eq<Sys, float><<<grid, kBlock, 0, st>>>(u0, (float *)f, ncell, Pd, cnt);
     return cudaGetLastError();
 }
 
@@ -49,8 +100,9 @@ template <class Sys, int DIM>
 cudaError_t totals_family(bool fp64, const void *f, double *partials, double *out, int64_t nx, int64_t ny,
                           const Shift &sh, const Params &P, cudaStream_t st)
 {
-    if (fp64) k_totals_partial<Sys, DIM, double><<<kRedBlocks, kRedThreads, 0, st>>>((const double *)f, partials, nx, ny, sh, P);
-    else k_totals_partial<Sys, DIM, float><<<kRedBlocks, kRedThreads, 0, st>>>((const float *)f, partials, nx, ny, sh, P);
+    const ParamsR<double> Pd = params_as<double>(P);
+    if (fp64) k_totals_partial<Sys, DIM, double><<<kRedBlocks, kRedThreads, 0, st>>>((const double *)f, partials, nx, ny, sh, Pd);
+    else k_totals_partial<Sys, DIM, float><<<kRedBlocks, kRedThreads, 0, st>>>((const float *)f, partials, nx, ny, sh, Pd);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_totals_final<2 + Sys::M><<<1, kRedThreads, 0, st>>>(partials, out, kRedBlocks);

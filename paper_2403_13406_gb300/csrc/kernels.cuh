@@ -46,7 +46,7 @@ __device__ __forceinline__ void warp_count(bool flag, unsigned long long *counte
 
 // One relaxation of one cell (eq. relaxationDiscretizationOmega), in place.
 template <class Sys, class R, bool ENTROPIC, bool DIAG>
-__device__ __forceinline__ void relax_cell(const Params &P, R *f, int kind, bool &fallback, bool &increase,
+__device__ __forceinline__ void relax_cell(const ParamsR<R> &P, R *f, int kind, bool &fallback, bool &increase,
                                            R &omega_used)
 {
     constexpr int Q = Sys::Q, M = Sys::M;
@@ -71,7 +71,7 @@ __device__ __forceinline__ void relax_cell(const Params &P, R *f, int kind, bool
     R delta[Q * M];
 #pragma unroll
     for (int i = 0; i < Q * M; ++i) delta[i] = feq[i] - f[i];
-    R w = R(P.omega);
+    R w = P.omega;
     if constexpr (ENTROPIC && !Sys::LINEAR) {
         typename Sys::template Ctx<R> cx;
         Sys::template prepare<R>(P, u, delta, cx);
@@ -92,7 +92,7 @@ __device__ __forceinline__ void relax_cell(const Params &P, R *f, int kind, bool
 
 // Fused stage: pull-shift by sh (transport, eq. transportPhase) then relax.
 template <class Sys, int DIM, class R, bool ENTROPIC, bool DIAG>
-__global__ void __launch_bounds__(kBlock) k_stage(StageArgs<R> a, Params P)
+__global__ void __launch_bounds__(kBlock) k_stage(StageArgs<R> a, ParamsR<R> P)
 {
     constexpr int Q = Sys::Q, M = Sys::M;
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -130,10 +130,98 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageArgs<R> a, Params P)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Temporally blocked 1D composite step.  One block owns an output tile of T
+// cells and loads a window of W = T + 2H cells of every plane into shared
+// memory, H = sum |s_i| over the fused stages.  In shared memory the transport
+// is index arithmetic: population k of window cell j lives at circular slot
+// (j - o_k) mod W, and a stage adds sign_k s_i to o_k before relaxing every
+// cell in place (one thread per cell, so the in-place update is race free).
+// Values wrapping around the window edges are wrong, but after the stages
+// they have moved at most H cells inward, so the tile [H, H + T) is exact.
+// Global traffic per fused step: one read (plus the 2H halo) and one write of
+// the state instead of one per stage.
+// ---------------------------------------------------------------------------
+
+template <class R> struct FusedArgs {
+    const R *__restrict__ fin;
+    R *__restrict__ fout;
+    int64_t n;       // cells
+    int tile;        // T
+    Counters *cnt;
+};
+
+template <class Sys, class R, bool ENTROPIC>
+__global__ void __launch_bounds__(kBlock) k_step1d(FusedArgs<R> a, StageList sl, ParamsR<R> P)
+{
+    constexpr int Q = Sys::Q, M = Sys::M, NP = Q * M;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sm = reinterpret_cast<R *>(smem_raw);
+    const int64_t x0 = (int64_t)blockIdx.x * a.tile;
+    const int T = (int)min((int64_t)a.tile, a.n - x0);
+    const int H = sl.halo;
+    const int W = T + 2 * H;
+    // load the window (periodic)
+    for (int j = threadIdx.x; j < W; j += blockDim.x) {
+        int64_t gx = (x0 - H + j) % a.n;
+        if (gx < 0) gx += a.n;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) sm[p * W + j] = a.fin[(int64_t)p * a.n + gx];
+    }
+    __syncthreads();
+    int off[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) off[k] = 0;
+    for (int st = 0; st < sl.n; ++st) {
+        const int s = sl.shift[st], kind = sl.kind[st];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) off[k] += Lattice<1>::sign(k) * s;
+        const int jend = ((W + 31) / 32) * 32;  // whole warps for the warp-level counters
+        for (int j = threadIdx.x; j < jend; j += blockDim.x) {
+            const bool valid = j < W;
+            bool fb = false, inc = false;
+            if (valid) {
+                int slot[Q];
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    int i = j - off[k];
+                    i = i < 0 ? i + W : (i >= W ? i - W : i);
+                    slot[k] = i;
+                }
+                R f[NP];
+#pragma unroll
+                for (int k = 0; k < Q; ++k)
+#pragma unroll
+                    for (int m = 0; m < M; ++m) f[k * M + m] = sm[(k * M + m) * W + slot[k]];
+                R w;
+                relax_cell<Sys, R, ENTROPIC, false>(P, f, kind, fb, inc, w);
+                // only cells of the final tile count towards the fallback counter
+                fb = fb && j >= H && j < H + T;
+#pragma unroll
+                for (int k = 0; k < Q; ++k)
+#pragma unroll
+                    for (int m = 0; m < M; ++m) sm[(k * M + m) * W + slot[k]] = f[k * M + m];
+            }
+            if constexpr (ENTROPIC && !Sys::LINEAR) warp_count(fb, &a.cnt->fallbacks);
+        }
+        __syncthreads();
+    }
+    // write the exact tile
+    for (int j = threadIdx.x; j < T; j += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            int i = j + H - off[k];
+            i = i < 0 ? i + W : (i >= W ? i - W : i);
+#pragma unroll
+            for (int m = 0; m < M; ++m) a.fout[(int64_t)(k * M + m) * a.n + x0 + j] = sm[(k * M + m) * W + i];
+        }
+    }
+}
+
 // f_k = f^eq_k(u0) (Section 3.1) with the domain check of Section 1.2.
 template <class Sys, class R>
 __global__ void __launch_bounds__(kBlock) k_init_eq(const double *__restrict__ u0, R *__restrict__ f,
-                                                    int64_t ncell, Params P, Counters *cnt)
+                                                    int64_t ncell, ParamsR<double> P, Counters *cnt)
 {
     constexpr int Q = Sys::Q, M = Sys::M;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -200,7 +288,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(const R *__restrict__ f, doub
 // set of cells in a fixed tree order into partials[block][2 + M].
 template <class Sys, int DIM, class R>
 __global__ void __launch_bounds__(kRedThreads) k_totals_partial(const R *__restrict__ f, double *__restrict__ partials,
-                                                                int64_t nx, int64_t ny, Shift sh, Params P)
+                                                                int64_t nx, int64_t ny, Shift sh, ParamsR<double> P)
 {
     constexpr int Q = Sys::Q, M = Sys::M, NV = 2 + M;
     const int64_t ncell = nx * ny;

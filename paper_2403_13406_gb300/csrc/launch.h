@@ -22,6 +22,19 @@ struct StageLaunch {
 
 enum Family { FAM_LINEAR1, FAM_LINEAR2, FAM_BURGERS1, FAM_BURGERS2, FAM_SW1, FAM_SW2, FAM_EULER2 };
 
+struct FusedLaunch {
+    const void *fin;
+    void *fout;
+    int64_t n;
+    StageList sl;
+    Counters *cnt;
+    Params P;
+    cudaStream_t stream;
+};
+
+// temporally blocked 1D step (several stages in shared memory); 1D families only
+cudaError_t launch_fused1d(int family, bool fp64, bool entropic, const FusedLaunch &L);
+
 // fused pull-shift + relaxation stage
 cudaError_t launch_stage(int family, bool fp64, bool entropic, bool diag, const StageLaunch &L);
 // f = f^eq(u0) with the domain check

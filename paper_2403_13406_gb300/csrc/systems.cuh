@@ -19,6 +19,12 @@
 
 namespace eslbm {
 
+// Division in the kernel's arithmetic type: the FP32 path uses the fast
+// reciprocal-based division (a few ulp; far below the storage rounding of the
+// relaxed distributions), the FP64 path the correctly rounded one.
+template <class R> __device__ __forceinline__ R qdiv(R a, R b) { return a / b; }
+template <> __device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
+
 // ---------------------------------------------------------------------------
 // Scalar systems (M = 1): linear transport and Burgers.  Dual kinetic
 // entropies s*_k(p) = p^2/(2Q) + sign_k G^{j*}(p)/(2V) (Examples 1, 2, 4 and
@@ -35,14 +41,14 @@ template <int DIM, bool BURGERS> struct Scalar {
     static constexpr int M = 1;
     static constexpr bool LINEAR = !BURGERS;
 
-    template <class R> __device__ static R flux(const Params &P, int j, R u)
+    template <class R> __device__ static R flux(const ParamsR<R> &P, int j, R u)
     {
-        return BURGERS ? R(P.c[j]) * R(0.5) * u * u : R(P.a[j]) * u;
+        return BURGERS ? P.c[j] * R(0.5) * u * u : P.a[j] * u;
     }
 
-    template <class R> __device__ static void equilibrium(const Params &P, const R *u, R *feq)
+    template <class R> __device__ static void equilibrium(const ParamsR<R> &P, const R *u, R *feq)
     {
-        const R inv2V = R(0.5) / R(P.V);
+        const R inv2V = P.inv2V;
         const R phi0 = flux<R>(P, 0, u[0]);
         const R phi1 = DIM == 2 ? flux<R>(P, 1, u[0]) : R(0);
         const R base = u[0] / R(Q);
@@ -54,39 +60,39 @@ template <int DIM, bool BURGERS> struct Scalar {
     }
 
     // convexity of every s*_k at the equilibrium dual p = u
-    template <class R> __device__ static bool admissible(const Params &P, const R *u)
+    template <class R> __device__ static bool admissible(const ParamsR<R> &P, const R *u)
     {
 #pragma unroll
         for (int j = 0; j < DIM; ++j) {
-            const R slope = BURGERS ? R(P.c[j]) * u[0] : R(P.a[j]);
-            if (!(fabs(slope) * R(Q) < R(2) * R(P.V))) return false;
+            const R slope = BURGERS ? P.c[j] * u[0] : P.a[j];
+            if (!(fabs(slope) * R(Q) < R(2) * P.V)) return false;
         }
         return isfinite(u[0]);
     }
 
-    template <class R> __device__ static R entropy(const Params &, const R *u) { return R(0.5) * u[0] * u[0]; }
+    template <class R> __device__ static R entropy(const ParamsR<R> &, const R *u) { return R(0.5) * u[0] * u[0]; }
 
     template <class R> struct Ctx {
         R D2[Q], b12[Q], d[Q];
     };
 
-    template <class R> __device__ static void prepare(const Params &P, const R *u, const R *delta, Ctx<R> &cx)
+    template <class R> __device__ static void prepare(const ParamsR<R> &P, const R *u, const R *delta, Ctx<R> &cx)
     {
         const R p = u[0];
-        const R inv2V = R(0.5) / R(P.V);
+        const R inv2V = P.inv2V;
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const int j = Lattice<DIM>::axis(k);
             const R sg = R(Lattice<DIM>::sign(k));
-            const R slope = BURGERS ? R(P.c[j]) * p : R(P.a[j]);
+            const R slope = BURGERS ? P.c[j] * p : P.a[j];
             cx.D2[k] = R(1) / R(Q) + sg * slope * inv2V;
-            cx.b12[k] = BURGERS ? sg * R(P.c[j]) / R(P.V) : R(0);
+            cx.b12[k] = BURGERS ? sg * P.c[j] * (R(2) * inv2V) : R(0);
             cx.d[k] = delta[k];
         }
     }
 
     // B = sum_k B_k(t delta_k), dB = d B / dt.  false outside the convexity domain.
-    template <class R> __device__ static bool eval(const Params &, const Ctx<R> &cx, R t, R &B, R &dB)
+    template <class R> __device__ static bool eval(const ParamsR<R> &, const Ctx<R> &cx, R t, R &B, R &dB)
     {
         B = R(0);
         dB = R(0);
@@ -126,11 +132,11 @@ template <int DIM> struct ShallowWater {
     static constexpr int M = DIM + 1;
     static constexpr bool LINEAR = false;
 
-    template <class R> __device__ static void equilibrium(const Params &P, const R *u, R *feq)
+    template <class R> __device__ static void equilibrium(const ParamsR<R> &P, const R *u, R *feq)
     {
         const R h = u[0];
-        const R g = R(P.g);
-        const R inv2V = R(0.5) / R(P.V);
+        const R g = P.g;
+        const R inv2V = P.inv2V;
         const R hp = R(0.5) * g * h * h;
         R phi[2][3];
         const R vx = u[1] / h;
@@ -156,12 +162,12 @@ template <int DIM> struct ShallowWater {
     }
 
     // h > 0 and |v_j| + sqrt(g h) < 2V/Q along each axis (Example 3)
-    template <class R> __device__ static bool admissible(const Params &P, const R *u)
+    template <class R> __device__ static bool admissible(const ParamsR<R> &P, const R *u)
     {
         const R h = u[0];
         if (!(h > R(0)) || !isfinite(h)) return false;
-        const R cs = sqrt(R(P.g) * h);
-        const R nu = R(2) * R(P.V) / R(Q);
+        const R cs = sqrt(P.g * h);
+        const R nu = R(2) * P.V / R(Q);
 #pragma unroll
         for (int j = 0; j < DIM; ++j) {
             const R v = u[1 + j] / h;
@@ -170,108 +176,126 @@ template <int DIM> struct ShallowWater {
         return true;
     }
 
-    template <class R> __device__ static R entropy(const Params &P, const R *u)
+    template <class R> __device__ static R entropy(const ParamsR<R> &P, const R *u)
     {
         R q2 = u[1] * u[1];
         if (DIM == 2) q2 += u[2] * u[2];
-        return R(0.5) * q2 / u[0] + R(0.5) * R(P.g) * u[0] * u[0];
+        return R(0.5) * q2 / u[0] + R(0.5) * P.g * u[0] * u[0];
     }
 
     template <class R> struct Ctx {
         R W, v[DIM], c[Q], f1[Q], d[Q][M];
+        R rc[Q];      // 1 / c_k
+        R rg0[Q];     // 1 / (f^eq_1 (W/(2c^2) - 1)): slope of the linearised equation in b
     };
 
-    template <class R> __device__ static void prepare(const Params &P, const R *u, const R *delta, Ctx<R> &cx)
+    template <class R> __device__ static void prepare(const ParamsR<R> &P, const R *u, const R *delta, Ctx<R> &cx)
     {
         const R h = u[0];
-        cx.W = R(2) * R(P.g) * h;
+        cx.W = R(2) * P.g * h;
+        const R rh = R(1) / h;
 #pragma unroll
-        for (int j = 0; j < DIM; ++j) cx.v[j] = u[1 + j] / h;
-        const R nu = R(2) * R(P.V) / R(Q);
-        const R inv2V = R(0.5) / R(P.V);
+        for (int j = 0; j < DIM; ++j) cx.v[j] = u[1 + j] * rh;
+        const R nu = R(2) * P.V / R(Q);
+        const R inv2V = P.inv2V;
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const int dax = Lattice<DIM>::axis(k);
             const R sg = R(Lattice<DIM>::sign(k));
-            cx.c[k] = nu + sg * cx.v[dax];
-            cx.f1[k] = h * cx.c[k] * inv2V;  // f^eq_1 of population k
+            const R ck = nu + sg * cx.v[dax];
+            cx.c[k] = ck;
+            cx.f1[k] = h * ck * inv2V;  // f^eq_1 of population k
+            cx.rc[k] = qdiv(R(1), ck);  // only seeds the Newton guess
+            cx.rg0[k] = qdiv(R(1), cx.f1[k] * (R(0.5) * cx.W * cx.rc[k] * cx.rc[k] - R(1)));
 #pragma unroll
             for (int m = 0; m < M; ++m) cx.d[k][m] = delta[k * M + m];
         }
     }
 
-    template <class R> __device__ static bool eval(const Params &P, const Ctx<R> &cx, R t, R &B, R &dB)
+    template <class R> __device__ static bool eval(const ParamsR<R> &P, const Ctx<R> &cx, R t, R &B, R &dB)
     {
-        const R g = R(P.g), V = R(P.V);
-        const R gV4 = R(4) * g * V;
-        const R inv16gV = R(1) / (R(16) * g * V);
+        constexpr bool FAST = sizeof(R) == 4;
+        const R gV4 = P.gV4;
+        const R inv16gV = P.inv16gV;
         const R W = cx.W;
+        bool good = true;
+        R h1[Q], r[Q], f1p[Q], b[Q], bscale[Q], db[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int dax = Lattice<DIM>::axis(k);
+            const R sg = R(Lattice<DIM>::sign(k));
+            h1[k] = t * cx.d[k][0];
+            const R hd = t * cx.d[k][1 + dax];
+            f1p[k] = cx.f1[k] + h1[k];
+            good &= f1p[k] > R(0);
+            r[k] = hd - cx.v[dax] * h1[k];
+            // linearised guess at b = 0; the magnitude of its two terms is the convergence
+            // scale of b (which itself can be far smaller when they cancel)
+            const R lin = R(0.5) * sg * W * h1[k] * cx.rc[k];
+            b[k] = (r[k] - lin) * cx.rg0[k];
+            bscale[k] = (fabs(r[k]) + fabs(lin)) * fabs(cx.rg0[k]);
+            db[k] = R(0);
+        }
+        // one Newton step on G(b) = -b f'_1 - sign dW (2W - dW)/(16 g V) - r for population k
+        auto newton = [&](int k) {
+            const R sg = R(Lattice<DIM>::sign(k));
+            const R cp = cx.c[k] - sg * b[k];
+            const R rcp = qdiv(R(1), cp);
+            const R dW = -(gV4 * h1[k] + sg * b[k] * W) * rcp;
+            const R Wp = W - dW;
+            const R G = -b[k] * f1p[k] - sg * dW * (W + Wp) * inv16gV - r[k];
+            const R Gp = f1p[k] * (R(0.5) * Wp * rcp * rcp - R(1));
+            good &= (cp > R(0)) & (Wp > R(0)) & (Gp < R(0));
+            db[k] = qdiv(G, Gp);
+            b[k] -= db[k];
+        };
+        // min_inner steps for every population, in lockstep: straight-line code that the
+        // scheduler can interleave across populations, and no divergence for smooth cells
+#pragma unroll
+        for (int it = 0; it < Tol<R>::min_inner; ++it)
+#pragma unroll
+            for (int k = 0; k < Q; ++k) newton(k);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            R prev = fabs(db[k]);
+            bool conv = prev <= Tol<R>::inner * (fabs(b[k]) + bscale[k]);
+            for (int it = Tol<R>::min_inner; !conv && it < Tol<R>::max_inner; ++it) {
+                newton(k);
+                const R ad = fabs(db[k]);
+                if (ad <= Tol<R>::inner * (fabs(b[k]) + bscale[k])) {
+                    conv = true;
+                } else if (ad >= prev) {  // stalled at the rounding level
+                    conv = ad <= Tol<R>::inner_accept * (fabs(b[k]) + bscale[k]);
+                    break;
+                }
+                prev = ad;
+            }
+            if (FAST && !conv) conv = fabs(db[k]) <= Tol<R>::inner_accept * (fabs(b[k]) + bscale[k]);
+            good &= conv;
+        }
         B = R(0);
         dB = R(0);
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const int dax = Lattice<DIM>::axis(k);
             const R sg = R(Lattice<DIM>::sign(k));
-            const R h1 = t * cx.d[k][0];
-            const R hd = t * cx.d[k][1 + dax];
-            R ht = R(0);
-            if (DIM == 2) ht = t * cx.d[k][2 - dax];
-            if (h1 == R(0) && hd == R(0) && ht == R(0)) continue;
-            const R vd = cx.v[dax];
             const R ck = cx.c[k];
-            const R f1p = cx.f1[k] + h1;
-            if (!(f1p > R(0))) return false;
-            const R r = hd - vd * h1;
-            // linearised guess at b = 0
-            const R A0 = W / (R(2) * ck * ck) - R(1);
-            const R lin = sg * W * h1 / (R(2) * ck);
-            R b = (r - lin) / (cx.f1[k] * A0);
-            // magnitude of the two terms of the guess: the convergence scale of b, which
-            // itself can be far smaller when they cancel
-            const R bscale = (fabs(r) + fabs(lin)) / (cx.f1[k] * fabs(A0));
-            R cp, dW, Wp, rcp;
-            bool conv = false;
-            R prev = R(INFINITY);
-            for (int it = 0; it < Tol<R>::max_inner; ++it) {
-                cp = ck - sg * b;
-                if (!(cp > R(0))) return false;
-                rcp = R(1) / cp;
-                dW = -(gV4 * h1 + sg * b * W) * rcp;
-                Wp = W - dW;
-                if (!(Wp > R(0))) return false;
-                const R G = -b * f1p - sg * dW * (W + Wp) * inv16gV - r;
-                const R Gp = f1p * (R(0.5) * Wp * rcp * rcp - R(1));
-                if (!(Gp < R(0))) return false;
-                const R db = G / Gp;
-                b -= db;
-                const R ad = fabs(db);
-                // at least min_inner steps for every lane, so that a warp of smooth cells leaves
-                // the loop together
-                if (it + 1 >= Tol<R>::min_inner && ad <= Tol<R>::inner * (fabs(b) + bscale)) {
-                    conv = true;
-                    break;
-                }
-                if (it >= Tol<R>::min_inner && ad >= prev) {  // stalled at the rounding level
-                    conv = ad <= Tol<R>::inner_accept * (fabs(b) + bscale);
-                    break;
-                }
-                prev = ad;
+            const R cp = ck - sg * b[k];
+            const R dW = -(gV4 * h1[k] + sg * b[k] * W) * qdiv(R(1), cp);
+            const R Wp = W - dW;
+            R ct = R(0), vt = R(0);
+            if (DIM == 2) {
+                vt = cx.v[1 - dax];
+                ct = qdiv(vt * h1[k] - t * cx.d[k][2 - dax], f1p[k]);
             }
-            if (!conv) return false;
-            cp = ck - sg * b;
-            dW = -(gV4 * h1 + sg * b * W) / cp;
-            Wp = W - dW;
-            R ct = R(0);
-            if (DIM == 2) ct = (cx.v[1 - dax] * h1 - ht) / f1p;
-            R vt = R(0);
-            if (DIM == 2) vt = cx.v[1 - dax];
-            const R D1 = R(0.5) * (dW - R(2) * vd * b + b * b - R(2) * vt * ct + ct * ct);
-            B += (ck * dW * dW + R(2) * Wp * (cp * (b * b + ct * ct) + sg * b * dW)) * inv16gV;
-            R dot = D1 * cx.d[k][0] + b * cx.d[k][1 + dax];
+            const R bk = b[k];
+            const R D1 = R(0.5) * (dW - R(2) * cx.v[dax] * bk + bk * bk - R(2) * vt * ct + ct * ct);
+            B += (ck * dW * dW + R(2) * Wp * (cp * (bk * bk + ct * ct) + sg * bk * dW)) * inv16gV;
+            R dot = D1 * cx.d[k][0] + bk * cx.d[k][1 + dax];
             if (DIM == 2) dot += ct * cx.d[k][2 - dax];
             dB -= dot;
         }
-        return true;
+        return good;
     }
 };
 
@@ -285,14 +309,14 @@ struct Euler2 {
     static constexpr int M = 4;
     static constexpr bool LINEAR = false;
 
-    template <class R> __device__ static void equilibrium(const Params &P, const R *u, R *feq)
+    template <class R> __device__ static void equilibrium(const ParamsR<R> &P, const R *u, R *feq)
     {
         const R rho = u[0], mx = u[1], my = u[2], E = u[3];
         const R vx = mx / rho, vy = my / rho;
-        const R p = R(P.gamma - 1.0) * (E - R(0.5) * (mx * vx + my * vy));
+        const R p = P.gamma_m1 * (E - R(0.5) * (mx * vx + my * vy));
         const R phx[4] = {mx, mx * vx + p, my * vx, vx * (E + p)};
         const R phy[4] = {my, mx * vy, my * vy + p, vy * (E + p)};
-        const R inv2V = R(0.5) / R(P.V);
+        const R inv2V = P.inv2V;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const R *phi = (k & 1) ? phy : phx;
@@ -305,21 +329,21 @@ struct Euler2 {
         }
     }
 
-    template <class R> __device__ static bool admissible(const Params &P, const R *u)
+    template <class R> __device__ static bool admissible(const ParamsR<R> &P, const R *u)
     {
         const R rho = u[0];
         if (!(rho > R(0))) return false;
-        const R p = R(P.gamma - 1.0) * (u[3] - R(0.5) * (u[1] * u[1] + u[2] * u[2]) / rho);
+        const R p = P.gamma_m1 * (u[3] - R(0.5) * (u[1] * u[1] + u[2] * u[2]) / rho);
         return p > R(0) && isfinite(p);
     }
 
-    template <class R> __device__ static R entropy(const Params &, const R *) { return R(NAN); }
+    template <class R> __device__ static R entropy(const ParamsR<R> &, const R *) { return R(NAN); }
 
     template <class R> struct Ctx {
         R unused;
     };
-    template <class R> __device__ static void prepare(const Params &, const R *, const R *, Ctx<R> &) {}
-    template <class R> __device__ static bool eval(const Params &, const Ctx<R> &, R, R &B, R &dB)
+    template <class R> __device__ static void prepare(const ParamsR<R> &, const R *, const R *, Ctx<R> &) {}
+    template <class R> __device__ static bool eval(const ParamsR<R> &, const Ctx<R> &, R, R &B, R &dB)
     {
         B = R(NAN);
         dB = R(NAN);
@@ -349,7 +373,7 @@ struct Euler2 {
 // ---------------------------------------------------------------------------
 
 template <class Sys, class R>
-__device__ R entropic_omega(const Params &P, const typename Sys::template Ctx<R> &cx, bool &fallback)
+__device__ R entropic_omega(const ParamsR<R> &P, const typename Sys::template Ctx<R> &cx, bool &fallback)
 {
     fallback = false;
     R Em, dEm;
@@ -358,7 +382,7 @@ __device__ R entropic_omega(const Params &P, const typename Sys::template Ctx<R>
         return R(1);
     }
     if (!(Em > R(0))) return R(2);  // at equilibrium (to rounding): every omega is the identity
-    R lo = R(0), hi = R(P.t_max);
+    R lo = R(0), hi = P.t_max;
     R Flo = -Em, Fhi = R(0);
     bool hi_ok = false;
     R t;
@@ -384,7 +408,7 @@ __device__ R entropic_omega(const Params &P, const typename Sys::template Ctx<R>
         for (int i = 0; i < 4; ++i) {
             const R m = tm * tm * (b2 + tm * (b3 + tm * b4)) - Em;
             const R dm = tm * (R(2) * b2 + tm * (R(3) * b3 + R(4) * b4 * tm));
-            tm -= m / dm;
+            tm -= qdiv(m, dm);
         }
         if (tm > lo && tm < hi) {
             t = tm;

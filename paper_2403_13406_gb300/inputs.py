@@ -125,6 +125,41 @@ def sw_random_2d(nx, ny, seed=SEED, h_amp=0.05, u_amp=0.05):
     return np.stack([h, h * u, h * v])
 
 
+def euler_vortex_2d(nx, ny, length=10.0, strength=5.0, gamma=1.4, u_inf=(1.0, 1.0), centre=(5.0, 5.0)):
+    """Isentropic vortex on [0, L]^2 (rho, rho u, rho v, E): background rho = p = 1, velocity u_inf;
+    it is advected without change of shape by u_inf."""
+    X, Y = grid_2d(nx, ny, length, length)
+    dx_, dy_ = X - centre[0], Y - centre[1]
+    r2 = dx_ * dx_ + dy_ * dy_
+    e = np.exp(0.5 * (1.0 - r2))
+    u = u_inf[0] - strength / (2 * np.pi) * e * dy_
+    v = u_inf[1] + strength / (2 * np.pi) * e * dx_
+    T = 1.0 - (gamma - 1.0) * strength ** 2 / (8 * gamma * np.pi ** 2) * e * e
+    rho = T ** (1.0 / (gamma - 1.0))
+    p = rho ** gamma
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    return np.stack([rho, rho * u, rho * v, E])
+
+
+def euler_riemann_2d(nx, ny, seed=SEED, lo=0.5, hi=1.5, vel=0.5, gamma=1.4):
+    """Four constant states with a seeded interface point in [0.3, 0.7]^2 (rho, p in [lo, hi],
+    velocities in [-vel, vel])."""
+    rng = np.random.default_rng(seed)
+    X, Y = grid_2d(nx, ny)
+    x0, y0 = rng.uniform(0.3, 0.7, 2)
+    out = np.zeros((4, ny, nx))
+    for qx in (0, 1):
+        for qy in (0, 1):
+            rho, p = rng.uniform(lo, hi, 2)
+            u, v = rng.uniform(-vel, vel, 2)
+            mask = ((X >= x0) == bool(qx)) & ((Y >= y0) == bool(qy))
+            out[0][mask] = rho
+            out[1][mask] = rho * u
+            out[2][mask] = rho * v
+            out[3][mask] = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    return out
+
+
 def batched_sizes(count=64, lo=256, hi=1024, seed=SEED):
     """Uneven (nx, ny) instance sizes drawn uniformly from [lo, hi]."""
     rng = np.random.default_rng(seed)

@@ -41,6 +41,10 @@ CASES = {
     "linear2d": (2, "linear", 300, 7, dict(V=1.0, a=(0.2, -0.15)), lambda nx, ny: inputs.linear_sine_2d(nx, ny)),
     "sw2d": (2, "sw", 33, 27, dict(V=8.0, g=9.81), lambda nx, ny: inputs.sw_random_2d(nx, ny, seed=6)),
 }
+EULER = {
+    "euler_vortex": (2, "euler", 40, 36, dict(V=8.0, gamma=1.4), lambda nx, ny: inputs.euler_vortex_2d(nx, ny)),
+    "euler_riemann": (2, "euler", 45, 33, dict(V=8.0, gamma=1.4), lambda nx, ny: inputs.euler_riemann_2d(nx, ny)),
+}
 
 
 def oracle_model(dim, system, nx, ny, kw, mode):
@@ -53,7 +57,7 @@ def gpu_sim(dim, system, nx, ny, kw, mode, precision, scheme="I", **extra):
 
 
 def run_pair(name, mode, precision, nsteps, scheme="I"):
-    dim, system, nx, ny, kw, init = CASES[name]
+    dim, system, nx, ny, kw, init = CASES[name] if name in CASES else EULER[name]
     u0 = init(nx, ny)
     m = oracle_model(dim, system, nx, ny, kw, mode)
     f_ref = O.init_equilibrium(m, u0)
@@ -129,6 +133,44 @@ def test_composite_fp32(name, mode):
 def test_scheme_variants_fp64(scheme, mode):
     f, ref, _, _ = run_pair("burgers1d_ragged", mode, "fp64", 3, scheme=scheme)
     assert rel_max(f, ref) <= FP64_TOL
+
+
+@pytest.mark.parametrize("name", list(EULER))
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("scheme", ["I", "III"])
+def test_euler_fixed_omega(name, precision, scheme):
+    """2D Euler with omega = 2 (Section 6.3 uses scheme III); parity with the oracle."""
+    f, ref, _, _ = run_pair(name, "fixed", precision, 3, scheme=scheme)
+    if precision == "fp64":
+        assert rel_max(f, ref) <= FP64_TOL
+    else:
+        assert rel_l2(f, ref) <= FP32_TOL
+
+
+@pytest.mark.parametrize("name", ["burgers1d_ragged", "sw1d", "linear1d"])
+@pytest.mark.parametrize("mode", ["fixed", "entropic"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("scheme", ["I", "III", "plain", "B"])
+def test_fused_1d_matches_per_stage_bitwise(name, mode, precision, scheme):
+    """The temporally blocked 1D kernel (all stages of a step in shared memory) performs the
+    same per-cell arithmetic as one launch per stage (the path taken with diagnostics on):
+    bit for bit with a fixed omega; with the entropic omega the root-finder is inlined into two
+    different kernels and the compiler may contract its products into FMAs differently, so the
+    two agree to rounding."""
+    dim, system, nx, ny, kw, init = CASES[name]
+    u0 = init(nx, ny)
+    outs = []
+    for diag in (False, True):
+        sim = gpu_sim(dim, system, nx, ny, kw, mode, precision, scheme, diagnostics=diag)
+        sim.init_equilibrium(u0)
+        sim.step(5)
+        sim.step(26)
+        outs.append(sim.distributions(host=True))
+        sim.close()
+    if mode == "fixed":
+        assert np.array_equal(outs[0], outs[1])
+    else:
+        assert rel_max(outs[0], outs[1]) <= (1e-13 if precision == "fp64" else 2e-6)
 
 
 def test_config1_burgers_n256():
