@@ -180,6 +180,29 @@ eslbm_status eslbm_read_totals(eslbm_handle *h, double *out, int32_t on_device);
 eslbm_status eslbm_get_diagnostics(eslbm_handle *h, eslbm_diagnostics *out);
 eslbm_status eslbm_reset_diagnostics(eslbm_handle *h);
 
+/* Totals of a caller-held state, for callers that cannot allocate device memory
+   (no counterpart in the paper).  eslbm_read_totals needs a handle, whose
+   workspace the caller must allocate; code that runs while a CUDA graph is being
+   captured, or a host that gives the library a fixed pre-sized pool, cannot.
+   This call allocates nothing: its scratch is a file-scope device array of
+   64 KiB (8 x 1024 partial sums plus 8 totals) that every device loading the
+   library keeps until the process exits.
+   cfg: the state's configuration; f: device buffer of planes * ncell values in the
+   storage precision (16-byte aligned), physical layout; pending_shift: transport
+   still to apply (the totals are those of T(pending_shift) f); out: 2 + M doubles
+   as in eslbm_read_totals, device memory if out_on_device, else host memory (the
+   call then synchronizes the stream).  Same fixed-order reduction as
+   eslbm_read_totals.
+   The first call on a device looks up the scratch's device address on the current
+   device; make that first call before any stream capture.  All calls share the
+   scratch (it keeps the last call's contents; every call overwrites what it reads),
+   so calls that overlap on the GPU, e.g. on two streams, race.
+   Errors: ESLBM_ERR_ARG for a bad cfg, a null or misaligned pointer, or totals that
+   do not fit the scratch (more than 8, i.e. M > 6); ESLBM_ERR_CUDA on a failed
+   CUDA call. */
+eslbm_status eslbm_read_totals_noalloc(const eslbm_config *cfg, const void *f, int64_t pending_shift,
+                                       double *out, int32_t out_on_device, void *stream);
+
 /* Capture the launches of one step (two for an odd number of stages) in a CUDA
    graph and replay it inside eslbm_step (enable = 1), or launch directly
    (enable = 0, the default). */

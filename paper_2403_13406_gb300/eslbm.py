@@ -25,7 +25,8 @@ RELAX_MAIN, RELAX_PROJECT = 0, 1
 EXPORTS = ("eslbm_abi_version", "eslbm_status_string", "eslbm_query", "eslbm_create", "eslbm_destroy",
            "eslbm_set_stream", "eslbm_last_error", "eslbm_init_equilibrium", "eslbm_init_distributions",
            "eslbm_step", "eslbm_transport", "eslbm_relax", "eslbm_read_moments", "eslbm_read_distributions",
-           "eslbm_read_totals", "eslbm_get_diagnostics", "eslbm_reset_diagnostics", "eslbm_use_graph")
+           "eslbm_read_totals", "eslbm_get_diagnostics", "eslbm_reset_diagnostics", "eslbm_use_graph",
+           "eslbm_read_totals_noalloc")
 
 
 class Config(ctypes.Structure):
@@ -82,6 +83,7 @@ def lib():
         "eslbm_get_diagnostics": (ctypes.c_int, [H, ctypes.POINTER(Diagnostics)]),
         "eslbm_reset_diagnostics": (ctypes.c_int, [H]),
         "eslbm_use_graph": (ctypes.c_int, [H, i32]),
+        "eslbm_read_totals_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), vp, i64, vp, i32, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -125,6 +127,14 @@ def query(cfg):
     if st != OK:
         raise EslbmError(st, lib().eslbm_status_string(st).decode())
     return sz
+
+
+def read_totals_noalloc(cfg, f_ptr, pending_shift, out, out_on_device, stream_handle):
+    """Totals of a caller-held state without any allocation (see include/eslbm.h)."""
+    st = lib().eslbm_read_totals_noalloc(ctypes.byref(cfg), f_ptr, int(pending_shift), out, int(out_on_device),
+                                         stream_handle)
+    if st != OK:
+        raise EslbmError(st, lib().eslbm_status_string(st).decode())
 
 
 class Simulation:
