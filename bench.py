@@ -36,6 +36,12 @@ UNIT = "site_updates/s"
 N_CELLS = 1 << 20
 V, G, T_FINAL = 4.0, 9.81, 0.05
 L2_FLUSH_BYTES = 512 << 20
+# FP32 roofline of the dominant kernel (the fused composite step k_step1d, entropic shallow water):
+# 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz; and the FP32 operations of one cell-stage
+# (FADD + FMUL + 2 FFMA counted by ncu on this workload: 12.5e9 flops per launch over
+# 607 blocks x 1800 window cells x 18 stages)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FLOPS_PER_CELL_STAGE = 636.0
 
 
 def parse():
@@ -199,7 +205,7 @@ def main():
         tot = torch.empty(2 + sim.M, dtype=torch.float64, device=dev)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stages = int(sim.sizes.stages_per_step) * n_steps
-    launches_per_step = 1 + stages + 1 + 2  # init, stages, moments gather, totals (2 passes)
+    launches_per_step = 1 + n_steps + 1 + 2  # init, one fused launch per composite step, gather, totals
 
     def solve(ev=None):
         sim.init_equilibrium(u0)
@@ -235,14 +241,25 @@ def main():
     stage_ms = [e[1].elapsed_time(e[2]) / stages for e in evs]
     value, total_ms = aggregate(sum(step_ms), N * n_steps * args.steps, dist, dev)
 
-    # dominant kernel: the fused stage (moves every distribution in and out once)
-    bytes_per_stage = 2 * int(sim.sizes.planes) * N * 4
+    # dominant kernel: the fused composite step (one launch per composite step of 18 stages); it is
+    # bound by FP32 arithmetic (the entropic root-find), its global traffic being one read and one
+    # write of the 16 MB state per launch
     stage_s = statistics.mean(stage_ms) * 1e-3
+    launch_s = stage_s * int(sim.sizes.stages_per_step)
+    flops = FLOPS_PER_CELL_STAGE * N * int(sim.sizes.stages_per_step)
+    achieved = flops / launch_s / 1e12
     peak, peak_kind = peaks()
-    achieved = bytes_per_stage / stage_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": peak_kind, "kernel": "k_stage<ShallowWater<1>, fp32, entropic>",
-                "stage_us": stage_s * 1e6}
+    hbm_bytes = 2 * int(sim.sizes.planes) * N * 4
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": 16.8e6,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "kernel": "k_step1d<ShallowWater<1>, float, entropic> (one composite step per launch)",
+                "launch_us": launch_s * 1e6, "stage_us": stage_s * 1e6,
+                "flops_per_cell_stage": FLOPS_PER_CELL_STAGE,
+                "hbm_view": {"bytes_per_launch": hbm_bytes, "achieved_gbs": hbm_bytes / launch_s / 1e9,
+                             "peak_gbs": peak, "frac": hbm_bytes / launch_s / 1e9 / peak,
+                             "per_stage_model_gbs": 18 * hbm_bytes / launch_s / 1e9,
+                             "peak_source": peak_kind}}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     u0_pin = torch.from_numpy(u0_host).pin_memory()
