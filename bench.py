@@ -285,6 +285,7 @@ def main():
     extras = {}
     if not args.no_extras and rank == 0:
         extras = fp64_leg(sim, torch, eslbm, inputs, stream, dev, N)
+        extras.update(adjoint_leg(torch, eslbm, inputs, stream, dev))
     cpu = None
     if rank == 0 and world == 1 and not args.no_extras:
         rate, dt = oracle_sample(2048)
@@ -343,6 +344,32 @@ def fp64_leg(sim32, torch, eslbm, inputs, stream, dev, N, nsteps=60):
     out["fp32_composite"]["rel_l2_h_vs_fp64"] = float(np.linalg.norm(res["fp32_composite"][0] - ref) / nrm)
     out["fp64_plain"]["rel_l2_h_vs_fp64_composite"] = float(np.linalg.norm(res["fp64_plain"][0] - ref) / nrm)
     return {"fp32_vs_fp64": {"N": N, "t": nsteps * 24.0 / N / V, **out}}
+
+
+def adjoint_leg(torch, eslbm, inputs, stream, dev, N=1 << 16, n=96, K=16):
+    """Reverse mode against forward on the same workload shape (1D shallow water, FP32, entropic):
+    one forward solve (init, n steps, moments) and one eslbm_gradient (forward with checkpoints
+    every K steps, segment and step recomputation, adjoint stages)."""
+    cfg = eslbm.make_config(1, "sw", N, V=V, g=G, precision="fp32", omega_mode="entropic")
+    with torch.cuda.stream(stream):
+        sim = eslbm.Simulation(cfg, stream=stream, device=dev)
+        u0 = torch.from_numpy(inputs.sw_sine_1d(N, 1.0, 0.1)).to(dev)
+        lam = torch.ones((2, N), dtype=torch.float64, device=dev)
+        times = {}
+        for name in ("forward", "adjoint", "forward", "adjoint"):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            if name == "forward":
+                sim.init_equilibrium(u0)
+                sim.step(n)
+                sim.moments()
+            else:
+                sim.gradient(u0, lam, n, K)
+            torch.cuda.synchronize(dev)
+            times[name] = time.perf_counter() - t0
+        sim.close()
+    return {"adjoint_vs_forward": {"N": N, "steps": n, "checkpoint_every": K, "forward_s": times["forward"],
+                                   "adjoint_s": times["adjoint"], "ratio": times["adjoint"] / times["forward"]}}
 
 
 if __name__ == "__main__":

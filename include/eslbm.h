@@ -203,6 +203,26 @@ eslbm_status eslbm_reset_diagnostics(eslbm_handle *h);
 eslbm_status eslbm_read_totals_noalloc(const eslbm_config *cfg, const void *f, int64_t pending_shift,
                                        double *out, int32_t out_on_device, void *stream);
 
+/* Bytes of the device workspace eslbm_gradient needs for n steps checkpointed
+   every K steps: (ceil(n/K) + min(K, n) + stages_per_step + 2) state buffers,
+   each rounded up to 256 bytes. */
+eslbm_status eslbm_gradient_workspace(const eslbm_config *cfg, int64_t n, int64_t K, uint64_t *bytes);
+
+/* Reverse mode (no counterpart in the paper, which does not differentiate the
+   scheme): gradient dJ/du0 of a scalar J(u_T) for u_T = the moments after n steps
+   of the configured scheme from f_0 = f^eq(u0).  u0, dJ_duT, dJ_du0: M double
+   planes in device memory.  The forward pass keeps the state every K steps in ws;
+   the reverse pass recomputes each K-step segment (keeping every step's starting
+   state), then each step stage by stage (keeping every stage's input), and applies
+   the adjoint stages in reverse: the reverse shift of the transport and the
+   transposed Jacobian of the relaxation, including the derivative of the entropic
+   omega by the implicit function theorem on eq. variableOmegaProblem.  On return
+   the handle holds the final forward state.  ws: device workspace of at least
+   eslbm_gradient_workspace bytes, 256-byte aligned.  Synchronizes (the forward
+   init checks the domain). */
+eslbm_status eslbm_gradient(eslbm_handle *h, const double *u0, const double *dJ_duT, double *dJ_du0, int64_t n,
+                            int64_t K, void *ws, uint64_t ws_bytes);
+
 /* Capture the launches of one step (two for an odd number of stages) in a CUDA
    graph and replay it inside eslbm_step (enable = 1), or launch directly
    (enable = 0, the default). */

@@ -345,11 +345,148 @@ eslbm_status capture_graph(eslbm_handle *h)
     return ESLBM_OK;
 }
 
+// ---- reverse mode -----------------------------------------------------------
+
+uint64_t slot_stride(const eslbm_handle *h) { return (h->sz.state_bytes + 255u) / 256u * 256u; }
+
+struct GradLayout {
+    int64_t n_outer, inner, stages;
+    uint64_t stride, bytes;
+};
+
+GradLayout grad_layout(const eslbm_sizes &sz, int64_t n, int64_t K)
+{
+    GradLayout g;
+    g.n_outer = n > 0 ? (n + K - 1) / K : 1;
+    g.inner = std::min<int64_t>(K, std::max<int64_t>(n, 1));
+    g.stages = sz.stages_per_step;
+    g.stride = (sz.state_bytes + 255u) / 256u * 256u;
+    g.bytes = g.stride * (uint64_t)(g.n_outer + g.inner + g.stages + 2);
+    return g;
+}
+
+struct RecordedStage {
+    const void *fin;
+    int64_t shift;
+    int kind;
+};
+
+eslbm_status stage_between(eslbm_handle *h, const void *fin, void *fout, int64_t shift, int kind)
+{
+    StageLaunch L;
+    L.fin = fin;
+    L.fout = fout;
+    L.nx = h->cfg.nx;
+    L.ny = h->cfg.ny;
+    L.ncell = h->sz.ncell;
+    L.sh = make_shift(h, shift);
+    L.kind = kind;
+    L.cnt = h->counters();
+    L.P = h->P;
+    L.stream = h->stream;
+    CK(launch_stage(h->family, h->fp64, h->cfg.omega_mode == ESLBM_OMEGA_ENTROPIC, false, L), "stage launch");
+    return ESLBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 int32_t eslbm_abi_version(void) { return ESLBM_ABI_VERSION; }
+
+eslbm_status eslbm_gradient_workspace(const eslbm_config *cfg, int64_t n, int64_t K, uint64_t *bytes)
+{
+    if (!bytes || n < 0 || K < 1) return ESLBM_ERR_ARG;
+    eslbm_sizes sz;
+    eslbm_status s = eslbm_query(cfg, &sz);
+    if (s != ESLBM_OK) return s;
+    *bytes = grad_layout(sz, n, K).bytes;
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_gradient(eslbm_handle *h, const double *u0, const double *dJ_duT, double *dJ_du0, int64_t n,
+                            int64_t K, void *ws, uint64_t ws_bytes)
+{
+    if (!h || !u0 || !dJ_duT || !dJ_du0 || !ws || n < 0 || K < 1) return fail(h, ESLBM_ERR_ARG, "bad argument");
+    const GradLayout G = grad_layout(h->sz, n, K);
+    if (ws_bytes < G.bytes || ((uintptr_t)ws & 255u)) return fail(h, ESLBM_ERR_ARG, "gradient workspace too small");
+    char *base = (char *)ws;
+    auto outer = [&](int64_t i) { return (void *)(base + G.stride * (uint64_t)i); };
+    auto inner = [&](int64_t i) { return (void *)(base + G.stride * (uint64_t)(G.n_outer + i)); };
+    auto stage = [&](int64_t i) { return (void *)(base + G.stride * (uint64_t)(G.n_outer + G.inner + i)); };
+    void *cot[2] = {base + G.stride * (uint64_t)(G.n_outer + G.inner + G.stages),
+                    base + G.stride * (uint64_t)(G.n_outer + G.inner + G.stages + 1)};
+    const size_t sb = (size_t)h->sz.state_bytes;
+
+    // forward pass, checkpoint every K steps (physical state and its pending shift)
+    eslbm_status s = eslbm_init_equilibrium(h, u0, 1);
+    if (s != ESLBM_OK) return s;
+    std::vector<int64_t> ck_pending((size_t)G.n_outer, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (i % K == 0) {
+            CK(cudaMemcpyAsync(outer(i / K), h->f[h->cur], sb, cudaMemcpyDeviceToDevice, h->stream), "checkpoint");
+            ck_pending[(size_t)(i / K)] = h->pending;
+        }
+        if ((s = run_ops(h)) != ESLBM_OK) return s;
+    }
+    // cotangent of the final physical state from the cotangent of the moments
+    int g = 0;
+    CK(launch_adjoint_readout(h->cfg.dim, h->fp64, dJ_duT, cot[g], h->cfg.nx, h->cfg.ny, (int)h->sz.M,
+                              make_shift(h, h->pending), h->stream),
+       "adjoint readout");
+    std::vector<int64_t> step_pending((size_t)G.inner, 0);
+    std::vector<RecordedStage> rec;
+    const bool entropic = h->cfg.omega_mode == ESLBM_OMEGA_ENTROPIC;
+    for (int64_t c = G.n_outer - 1; c >= 0 && n > 0; --c) {
+        const int64_t s0 = c * K, s1 = std::min(n, s0 + K);
+        // recompute the segment, keeping every step's starting state
+        CK(cudaMemcpyAsync(h->f[h->cur], outer(c), sb, cudaMemcpyDeviceToDevice, h->stream), "restore");
+        h->pending = ck_pending[(size_t)c];
+        for (int64_t j = 0; j < s1 - s0; ++j) {
+            CK(cudaMemcpyAsync(inner(j), h->f[h->cur], sb, cudaMemcpyDeviceToDevice, h->stream), "step state");
+            step_pending[(size_t)j] = h->pending;
+            if ((s = run_ops(h)) != ESLBM_OK) return s;
+        }
+        for (int64_t j = s1 - s0 - 1; j >= 0; --j) {
+            // recompute the step stage by stage, keeping every stage's input
+            rec.clear();
+            const void *in = inner(j);
+            int64_t pend = step_pending[(size_t)j];
+            for (const Op &op : h->ops) {
+                if (!op.relax) {
+                    pend += op.shift;
+                    continue;
+                }
+                void *out = stage((int64_t)rec.size());
+                if ((s = stage_between(h, in, out, pend, op.kind)) != ESLBM_OK) return s;
+                rec.push_back({in, pend, op.kind});
+                in = out;
+                pend = 0;
+            }
+            // reverse sweep of the stages: reverse shift and transposed relaxation Jacobian
+            for (int64_t st = (int64_t)rec.size() - 1; st >= 0; --st) {
+                AdjointLaunch A;
+                A.fin = rec[(size_t)st].fin;
+                A.gout = cot[g];
+                A.gin = cot[1 - g];
+                A.nx = h->cfg.nx;
+                A.ny = h->cfg.ny;
+                A.sh = make_shift(h, rec[(size_t)st].shift);
+                A.kind = rec[(size_t)st].kind;
+                A.P = h->P;
+                A.stream = h->stream;
+                CK(launch_adjoint_stage(h->family, h->fp64, entropic, A), "adjoint stage");
+                g = 1 - g;
+            }
+        }
+    }
+    CK(launch_adjoint_init(h->family, h->fp64, u0, cot[g], dJ_du0, h->sz.ncell, h->P, h->stream), "adjoint init");
+    // leave the handle on the final forward state
+    h->pending = 0;
+    s = eslbm_init_equilibrium(h, u0, 1);
+    if (s != ESLBM_OK) return s;
+    return eslbm_step(h, n);
+}
 
 const char *eslbm_status_string(eslbm_status s)
 {

@@ -74,6 +74,18 @@ struct StageList {
     int kind[kMaxFusedStages];   // KIND_MAIN or KIND_PROJECT
 };
 
+// Batched execution: independent instances of one system on grids of their own
+// size, packed in one pool per ping-pong side, cut into work items.
+struct BatchInstance {
+    int64_t nx, ny;
+    int64_t offset;  // element offset of the instance's first plane in the pool
+};
+struct BatchItem {
+    int32_t inst;    // instance
+    int32_t y;       // row
+    int32_t x0, nx;  // segment [x0, x0 + nx) of the row
+};
+
 // Device counters (first 64 bytes of the workspace).
 struct Counters {
     unsigned long long fallbacks;

@@ -83,6 +83,41 @@ cudaError_t launch_set(bool fp64, const double *src, void *f, int64_t n, Counter
     return cudaGetLastError();
 }
 
+cudaError_t adjoint_scalar(int, bool, bool, const AdjointLaunch &);
+cudaError_t adjoint_sw(int, bool, bool, const AdjointLaunch &);
+cudaError_t adjoint_init_scalar(int, bool, const double *, const void *, double *, int64_t, const Params &,
+                                cudaStream_t);
+cudaError_t adjoint_init_sw(int, bool, const double *, const void *, double *, int64_t, const Params &, cudaStream_t);
+
+cudaError_t launch_adjoint_stage(int family, bool fp64, bool entropic, const AdjointLaunch &L)
+{
+    if (family == FAM_SW1 || family == FAM_SW2) return adjoint_sw(family, fp64, entropic, L);
+    if (family == FAM_EULER2) return adjoint_family<Euler2, 2>(fp64, false, L);
+    return adjoint_scalar(family, fp64, entropic, L);
+}
+
+cudaError_t launch_adjoint_init(int family, bool fp64, const double *u0, const void *g, double *du0, int64_t ncell,
+                                const Params &P, cudaStream_t st)
+{
+    if (family == FAM_SW1 || family == FAM_SW2) return adjoint_init_sw(family, fp64, u0, g, du0, ncell, P, st);
+    if (family == FAM_EULER2) return adjoint_init_family<Euler2>(fp64, u0, g, du0, ncell, P, st);
+    return adjoint_init_scalar(family, fp64, u0, g, du0, ncell, P, st);
+}
+
+cudaError_t launch_adjoint_readout(int dim, bool fp64, const double *lam, void *g, int64_t nx, int64_t ny, int M,
+                                   const Shift &sh, cudaStream_t st)
+{
+    dim3 grid((unsigned)((nx + kBlock - 1) / kBlock), (unsigned)ny);
+    if (dim == 1) {
+        if (fp64) k_adjoint_readout<1, double><<<grid, kBlock, 0, st>>>(lam, (double *)g, nx, ny, M, sh);
+        else k_adjoint_readout<1, float><<<grid, kBlock, 0, st>>>(lam, (float *)g, nx, ny, M, sh);
+    } else {
+        if (fp64) k_adjoint_readout<2, double><<<grid, kBlock, 0, st>>>(lam, (double *)g, nx, ny, M, sh);
+        else k_adjoint_readout<2, float><<<grid, kBlock, 0, st>>>(lam, (float *)g, nx, ny, M, sh);
+    }
+    return cudaGetLastError();
+}
+
 int totals_blocks() { return kRedBlocks; }
 
 }  // namespace eslbm

@@ -21,6 +21,29 @@ cudaError_t fused_scalar(int family, bool fp64, bool entropic, const FusedLaunch
     return cudaErrorInvalidValue;
 }
 
+cudaError_t adjoint_scalar(int family, bool fp64, bool entropic, const AdjointLaunch &L)
+{
+    switch (family) {
+    case FAM_LINEAR1: return adjoint_family<Scalar<1, false>, 1>(fp64, entropic, L);
+    case FAM_LINEAR2: return adjoint_family<Scalar<2, false>, 2>(fp64, entropic, L);
+    case FAM_BURGERS1: return adjoint_family<Scalar<1, true>, 1>(fp64, entropic, L);
+    case FAM_BURGERS2: return adjoint_family<Scalar<2, true>, 2>(fp64, entropic, L);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t adjoint_init_scalar(int family, bool fp64, const double *u0, const void *g, double *du0, int64_t ncell,
+                                const Params &P, cudaStream_t st)
+{
+    switch (family) {
+    case FAM_LINEAR1: return adjoint_init_family<Scalar<1, false>>(fp64, u0, g, du0, ncell, P, st);
+    case FAM_LINEAR2: return adjoint_init_family<Scalar<2, false>>(fp64, u0, g, du0, ncell, P, st);
+    case FAM_BURGERS1: return adjoint_init_family<Scalar<1, true>>(fp64, u0, g, du0, ncell, P, st);
+    case FAM_BURGERS2: return adjoint_init_family<Scalar<2, true>>(fp64, u0, g, du0, ncell, P, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t init_scalar(int family, bool fp64, const double *u0, void *f, int64_t ncell, const Params &P,
                         Counters *cnt, cudaStream_t st)
 {

@@ -16,6 +16,21 @@ cudaError_t fused_sw(int family, bool fp64, bool entropic, const FusedLaunch &L)
     return cudaErrorInvalidValue;
 }
 
+cudaError_t adjoint_sw(int family, bool fp64, bool entropic, const AdjointLaunch &L)
+{
+    if (family == FAM_SW1) return adjoint_family<ShallowWater<1>, 1>(fp64, entropic, L);
+    if (family == FAM_SW2) return adjoint_family<ShallowWater<2>, 2>(fp64, entropic, L);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t adjoint_init_sw(int family, bool fp64, const double *u0, const void *g, double *du0, int64_t ncell,
+                            const Params &P, cudaStream_t st)
+{
+    if (family == FAM_SW1) return adjoint_init_family<ShallowWater<1>>(fp64, u0, g, du0, ncell, P, st);
+    if (family == FAM_SW2) return adjoint_init_family<ShallowWater<2>>(fp64, u0, g, du0, ncell, P, st);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t init_sw(int family, bool fp64, const double *u0, void *f, int64_t ncell, const Params &P,
                     Counters *cnt, cudaStream_t st)
 {

@@ -85,6 +85,40 @@ cudaError_t fused_family(bool fp64, bool entropic, const FusedLaunch &L)
     }
 }
 
+template <class Sys, int DIM, class R>
+cudaError_t adjoint_prec(bool entropic, const AdjointLaunch &L)
+{
+    dim3 grid((unsigned)((L.nx + kBlock - 1) / kBlock), (unsigned)L.ny);
+    const ParamsR<R> P = params_as<R>(L.P);
+    if constexpr (!Sys::LINEAR && Sys::M != 4) {
+        if (entropic) {
+            k_adjoint_stage<Sys, DIM, R, true><<<grid, kBlock, 0, L.stream>>>((const R *)L.fin, (const R *)L.gout,
+                                                                             (R *)L.gin, L.nx, L.ny, L.sh, L.kind, P);
+            return cudaGetLastError();
+        }
+    }
+    (void)entropic;
+    k_adjoint_stage<Sys, DIM, R, false><<<grid, kBlock, 0, L.stream>>>((const R *)L.fin, (const R *)L.gout,
+                                                                      (R *)L.gin, L.nx, L.ny, L.sh, L.kind, P);
+    return cudaGetLastError();
+}
+
+template <class Sys, int DIM>
+cudaError_t adjoint_family(bool fp64, bool entropic, const AdjointLaunch &L)
+{
+    return fp64 ? adjoint_prec<Sys, DIM, double>(entropic, L) : adjoint_prec<Sys, DIM, float>(entropic, L);
+}
+
+template <class Sys>
+cudaError_t adjoint_init_family(bool fp64, const double *u0, const void *g, double *du0, int64_t ncell,
+                                const Params &P, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)((ncell + kBlock - 1) / kBlock);
+    if (fp64) k_adjoint_init<Sys, double><<<grid, kBlock, 0, st>>>(u0, (const double *)g, du0, ncell, params_as<double>(P));
+    else k_adjoint_init<Sys, float><<<grid, kBlock, 0, st>>>(u0, (const float *)g, du0, ncell, params_as<float>(P));
+    return cudaGetLastError();
+}
+
 template <class Sys>
 cudaError_t init_family(bool fp64, const double *u0, void *f, int64_t ncell, const Params &P, Counters *cnt,
                         cudaStream_t st)

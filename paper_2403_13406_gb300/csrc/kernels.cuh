@@ -7,7 +7,11 @@
 // of 32 elements (coalesced), also for the shifted pulls.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "systems.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace eslbm {
 
@@ -215,6 +219,241 @@ __global__ void __launch_bounds__(kBlock) k_step1d(FusedArgs<R> a, StageList sl,
 #pragma unroll
             for (int m = 0; m < M; ++m) a.fout[(int64_t)(k * M + m) * a.n + x0 + j] = sm[(k * M + m) * W + i];
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of one relaxation.  For f' = f + omega(f) delta, delta = f^eq(u) - f,
+// u = sum_k f_k, E_k = d f^eq_k / d u:
+//   J^T g'  at population j  =  (1 - omega) g'_j + omega sum_k E_k^T g'_k
+//                                + grad_{f_j} omega (delta . g').
+// For the entropic omega = 1 + t*, F(t*, f) = 0 with F(t, f) = B(t) - B(-1),
+// B(t) = sum_k B_k(t delta_k; u), gives by the implicit function theorem
+// grad_f t* = -grad_f F / F'(t*), where (Sigma_k delta_k = 0 removes the
+// dependence through the dual p) grad_{f_j} F = t Delta_j(t) + Delta_j(-1)
+//   - (1 + t) sum_k E_k^T Delta_k(t) and F'(t) = -sum_k Delta_k(t) . delta_k,
+// Delta_k(t) = p - p'_k the dual deviation at h = t delta_k.  Cells at
+// equilibrium, fallback cells (omega = 1) and quadratic entropies have a
+// locally constant omega and no such term.
+// ---------------------------------------------------------------------------
+template <class Sys, class R, bool ENTROPIC>
+__device__ __forceinline__ void relax_adjoint(const ParamsR<R> &P, const R *f, const R *gout, int kind, R *gin)
+{
+    constexpr int Q = Sys::Q, M = Sys::M;
+    R u[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        R s = f[m];
+#pragma unroll
+        for (int k = 1; k < Q; ++k) s += f[k * M + m];
+        u[m] = s;
+    }
+    R E[Q * M * M];
+    Sys::template equilibrium_jacobian<R>(P, u, E);
+    R a[M];  // sum_k E_k^T g'_k
+#pragma unroll
+    for (int n = 0; n < M; ++n) {
+        R s = R(0);
+#pragma unroll
+        for (int k = 0; k < Q; ++k)
+#pragma unroll
+            for (int m = 0; m < M; ++m) s += E[(k * M + m) * M + n] * gout[k * M + m];
+        a[n] = s;
+    }
+    if (kind == KIND_PROJECT) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k)
+#pragma unroll
+            for (int n = 0; n < M; ++n) gin[k * M + n] = a[n];
+        return;
+    }
+    R feq[Q * M], delta[Q * M];
+    Sys::template equilibrium<R>(P, u, feq);
+#pragma unroll
+    for (int i = 0; i < Q * M; ++i) delta[i] = feq[i] - f[i];
+    R w = P.omega;
+    bool varying = false;
+    typename Sys::template Ctx<R> cx;
+    if constexpr (ENTROPIC && !Sys::LINEAR) {
+        Sys::template prepare<R>(P, u, delta, cx);
+        bool fb = false;
+        w = entropic_omega<Sys, R>(P, cx, fb);
+        R E0, d0;
+        varying = !fb && Sys::template eval<R>(P, cx, R(-1), E0, d0) && E0 > R(0);
+    } else if constexpr (ENTROPIC) {
+        w = R(2);
+    }
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+#pragma unroll
+        for (int n = 0; n < M; ++n) gin[k * M + n] = (R(1) - w) * gout[k * M + n] + w * a[n];
+    if constexpr (ENTROPIC && !Sys::LINEAR) {
+        if (varying) {
+            const R t = w - R(1);
+            R Dt[Q * M], Dm[Q * M], B, dB, Bm, dBm;
+            const bool ok = Sys::template eval<R>(P, cx, t, B, dB, Dt) & Sys::template eval<R>(P, cx, R(-1), Bm, dBm, Dm);
+            R dg = R(0);
+#pragma unroll
+            for (int i = 0; i < Q * M; ++i) dg += delta[i] * gout[i];
+            if (ok && dB > R(0) && dg != R(0)) {
+                R c[M];  // sum_k E_k^T Delta_k(t)
+#pragma unroll
+                for (int n = 0; n < M; ++n) {
+                    R s = R(0);
+#pragma unroll
+                    for (int k = 0; k < Q; ++k)
+#pragma unroll
+                        for (int m = 0; m < M; ++m) s += E[(k * M + m) * M + n] * Dt[k * M + m];
+                    c[n] = s;
+                }
+                const R scale = -dg / dB;  // (delta . g') * (-1 / F'(t))
+#pragma unroll
+                for (int k = 0; k < Q; ++k)
+#pragma unroll
+                    for (int n = 0; n < M; ++n)
+                        gin[k * M + n] += scale * (t * Dt[k * M + n] + Dm[k * M + n] - (R(1) + t) * c[n]);
+            }
+        }
+    }
+}
+
+// Adjoint of a fused stage f_out(x) = R(f_in(src_k(x))): the cotangent of the
+// stage input at src_k(x) is (J_R(x)^T g_out(x))_k (the reverse shift; src_k is
+// a bijection, so every input cell receives exactly one contribution).
+template <class Sys, int DIM, class R, bool ENTROPIC>
+__global__ void __launch_bounds__(kBlock) k_adjoint_stage(const R *__restrict__ fin, const R *__restrict__ gout,
+                                                          R *__restrict__ gin, int64_t nx, int64_t ny, Shift sh,
+                                                          int kind, ParamsR<R> P)
+{
+    constexpr int Q = Sys::Q, M = Sys::M;
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t y = blockIdx.y;
+    if (x >= nx) return;
+    const int64_t ncell = nx * ny, o = y * nx + x;
+    int64_t src[Q];
+    R f[Q * M], go[Q * M], gi[Q * M];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        src[k] = src_cell<DIM>(k, x, y, nx, ny, sh);
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            f[k * M + m] = fin[(int64_t)(k * M + m) * ncell + src[k]];
+            go[k * M + m] = gout[(int64_t)(k * M + m) * ncell + o];
+        }
+    }
+    relax_adjoint<Sys, R, ENTROPIC>(P, f, go, kind, gi);
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+#pragma unroll
+        for (int m = 0; m < M; ++m) gin[(int64_t)(k * M + m) * ncell + src[k]] = gi[k * M + m];
+}
+
+// Cotangent of the physical distributions from the cotangent of the moments
+// u(x) = sum_k f_k(src_k(x)) read with the pending shift sh.
+template <int DIM, class R>
+__global__ void __launch_bounds__(kBlock) k_adjoint_readout(const double *__restrict__ lam, R *__restrict__ g,
+                                                            int64_t nx, int64_t ny, int M, Shift sh)
+{
+    constexpr int Q = Lattice<DIM>::Q;
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t y = blockIdx.y;
+    if (x >= nx) return;
+    const int64_t ncell = nx * ny, o = y * nx + x;
+    for (int m = 0; m < M; ++m) {
+        const R l = R(lam[(int64_t)m * ncell + o]);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) g[(int64_t)(k * M + m) * ncell + src_cell<DIM>(k, x, y, nx, ny, sh)] = l;
+    }
+}
+
+// dJ/du0 = sum_k E_k(u0)^T g_k for f_0 = f^eq(u0)
+template <class Sys, class R>
+__global__ void __launch_bounds__(kBlock) k_adjoint_init(const double *__restrict__ u0, const R *__restrict__ g,
+                                                         double *__restrict__ du0, int64_t ncell, ParamsR<R> P)
+{
+    constexpr int Q = Sys::Q, M = Sys::M;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ncell) return;
+    R u[M], E[Q * M * M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) u[m] = R(u0[(int64_t)m * ncell + i]);
+    Sys::template equilibrium_jacobian<R>(P, u, E);
+#pragma unroll
+    for (int n = 0; n < M; ++n) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < Q; ++k)
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                s += double(E[(k * M + m) * M + n]) * double(g[(int64_t)(k * M + m) * ncell + i]);
+        du0[(int64_t)n * ncell + i] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batched persistent step: every instance of a batch advances through all the
+// stages of one composite step in a single cooperative launch.  A stage is a
+// sweep of the blocks over the work items (row segments of all instances,
+// each pulled periodically within its own instance); grid.sync() separates the
+// stages (the cooperative launch guarantees that all blocks are resident, and
+// fails instead of starting otherwise).  Ping-pong: stage i reads pool[i & 1]
+// and writes pool[(i + 1) & 1] relative to the entry side.
+// ---------------------------------------------------------------------------
+template <class R> struct BatchArgs {
+    R *pool[2];
+    const BatchInstance *inst;
+    const BatchItem *items;
+    int n_items;
+    int side;  // pool holding the state on entry
+    Counters *cnt;
+};
+
+template <class Sys, class R, bool ENTROPIC>
+__global__ void __launch_bounds__(kBlock) k_batch_step(BatchArgs<R> a, StageList sl, ParamsR<R> P)
+{
+    constexpr int Q = Sys::Q, M = Sys::M;
+    cg::grid_group grid = cg::this_grid();
+    int side = a.side;
+    for (int st = 0; st < sl.n; ++st) {
+        const R *__restrict__ fin = a.pool[side];
+        R *__restrict__ fout = a.pool[side ^ 1];
+        const int s = sl.shift[st], kind = sl.kind[st];
+        for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+            const BatchItem w = a.items[it];
+            const BatchInstance I = a.inst[w.inst];
+            const int64_t ncell = I.nx * I.ny;
+            const R *fi = fin + I.offset;
+            R *fo = fout + I.offset;
+            Shift sh;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const int64_t n = Lattice<2>::axis(k) == 0 ? I.nx : I.ny;
+                int64_t r = (-(int64_t)Lattice<2>::sign(k) * s) % n;
+                sh.roff[k] = r < 0 ? r + n : r;
+            }
+            for (int j = threadIdx.x; j < ((w.nx + 31) / 32) * 32; j += blockDim.x) {
+                const bool valid = j < w.nx;
+                bool fb = false, inc = false;
+                if (valid) {
+                    const int64_t x = w.x0 + j, y = w.y;
+                    R f[Q * M];
+#pragma unroll
+                    for (int k = 0; k < Q; ++k) {
+                        const int64_t src = src_cell<2>(k, x, y, I.nx, I.ny, sh);
+#pragma unroll
+                        for (int m = 0; m < M; ++m) f[k * M + m] = fi[(int64_t)(k * M + m) * ncell + src];
+                    }
+                    R wv;
+                    relax_cell<Sys, R, ENTROPIC, false>(P, f, kind, fb, inc, wv);
+                    const int64_t o = y * I.nx + x;
+#pragma unroll
+                    for (int i = 0; i < Q * M; ++i) fo[(int64_t)i * ncell + o] = f[i];
+                }
+                if constexpr (ENTROPIC && !Sys::LINEAR) warp_count(fb, &a.cnt->fallbacks);
+            }
+        }
+        side ^= 1;
+        grid.sync();
     }
 }
 

@@ -50,6 +50,26 @@ cudaError_t launch_gather_planes(int dim, bool fp64, const void *f, double *out,
                                  int plane0, int nplanes, const Shift &sh, cudaStream_t st);
 cudaError_t launch_set(bool fp64, const double *src, void *f, int64_t n, Counters *cnt, cudaStream_t st);
 
+struct AdjointLaunch {
+    const void *fin;   // forward input of the stage (physical layout)
+    const void *gout;  // cotangent of the stage output
+    void *gin;         // cotangent of the stage input (written)
+    int64_t nx, ny;
+    Shift sh;
+    int kind;
+    Params P;
+    cudaStream_t stream;
+};
+
+// reverse-mode stage (reverse shift + transposed relaxation Jacobian)
+cudaError_t launch_adjoint_stage(int family, bool fp64, bool entropic, const AdjointLaunch &L);
+// cotangent of the distributions from the cotangent of the moments (pending shift sh)
+cudaError_t launch_adjoint_readout(int dim, bool fp64, const double *lam, void *g, int64_t nx, int64_t ny, int M,
+                                   const Shift &sh, cudaStream_t st);
+// dJ/du0 from the cotangent of f_0 = f^eq(u0)
+cudaError_t launch_adjoint_init(int family, bool fp64, const double *u0, const void *g, double *du0, int64_t ncell,
+                                const Params &P, cudaStream_t st);
+
 int totals_blocks();
 
 }  // namespace eslbm

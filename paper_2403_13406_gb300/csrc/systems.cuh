@@ -60,6 +60,17 @@ template <int DIM, bool BURGERS> struct Scalar {
     }
 
     // convexity of every s*_k at the equilibrium dual p = u
+    // E[k] = d f^eq_k / d u
+    template <class R> __device__ static void equilibrium_jacobian(const ParamsR<R> &P, const R *u, R *E)
+    {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int j = Lattice<DIM>::axis(k);
+            const R slope = BURGERS ? P.c[j] * u[0] : P.a[j];
+            E[k] = R(1) / R(Q) + R(Lattice<DIM>::sign(k)) * slope * P.inv2V;
+        }
+    }
+
     template <class R> __device__ static bool admissible(const ParamsR<R> &P, const R *u)
     {
 #pragma unroll
@@ -91,14 +102,17 @@ template <int DIM, bool BURGERS> struct Scalar {
         }
     }
 
-    // B = sum_k B_k(t delta_k), dB = d B / dt.  false outside the convexity domain.
-    template <class R> __device__ static bool eval(const ParamsR<R> &, const Ctx<R> &cx, R t, R &B, R &dB)
+    // B = sum_k B_k(t delta_k), dB = d B / dt, and (if Dout) Delta_k = p - p'_k.
+    // false outside the convexity domain.
+    template <class R> __device__ static bool eval(const ParamsR<R> &, const Ctx<R> &cx, R t, R &B, R &dB,
+                                                   R *Dout = nullptr)
     {
         B = R(0);
         dB = R(0);
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const R h = t * cx.d[k];
+            if (Dout) Dout[k] = R(0);
             if (h == R(0)) continue;
             const R D2 = cx.D2[k], b12 = cx.b12[k];
             const R disc = D2 * D2 + b12 * h;
@@ -107,6 +121,7 @@ template <int DIM, bool BURGERS> struct Scalar {
             if (!(D2 - R(0.5) * b12 * Dl > R(0))) return false;  // s*'' at p - Delta
             B += Dl * Dl * (R(0.5) * D2 - b12 * Dl * R(1.0 / 6.0));
             dB -= Dl * cx.d[k];
+            if (Dout) Dout[k] = Dl;
         }
         return true;
     }
@@ -161,6 +176,35 @@ template <int DIM> struct ShallowWater {
         }
     }
 
+    // E[(k*M + m)*M + n] = d f^eq_{k,m} / d u_n
+    template <class R> __device__ static void equilibrium_jacobian(const ParamsR<R> &P, const R *u, R *E)
+    {
+        const R h = u[0], g = P.g;
+        R A[2][3][3];  // d phi^j / d u
+        const R vx = u[1] / h;
+        const R vy = DIM == 2 ? u[2] / h : R(0);
+        // phi^x = (q_x, q_x^2/h + g h^2/2, q_x q_y/h)
+        A[0][0][0] = R(0); A[0][0][1] = R(1); A[0][0][2] = R(0);
+        A[0][1][0] = g * h - vx * vx; A[0][1][1] = R(2) * vx; A[0][1][2] = R(0);
+        A[0][2][0] = -vx * vy; A[0][2][1] = vy; A[0][2][2] = vx;
+        // phi^y = (q_y, q_x q_y/h, q_y^2/h + g h^2/2)
+        A[1][0][0] = R(0); A[1][0][1] = R(0); A[1][0][2] = R(1);
+        A[1][1][0] = -vx * vy; A[1][1][1] = vy; A[1][1][2] = vx;
+        A[1][2][0] = g * h - vy * vy; A[1][2][1] = R(0); A[1][2][2] = R(2) * vy;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int j = Lattice<DIM>::axis(k);
+            const R s2V = R(Lattice<DIM>::sign(k)) * P.inv2V;
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+#pragma unroll
+                for (int n = 0; n < M; ++n) {
+                    // in 1D the second component is q_x: the flux rows/columns (0, 1) of phi^x
+                    E[(k * M + m) * M + n] = (m == n ? R(1) / R(Q) : R(0)) + s2V * A[j][m][n];
+                }
+        }
+    }
+
     // h > 0 and |v_j| + sqrt(g h) < 2V/Q along each axis (Example 3)
     template <class R> __device__ static bool admissible(const ParamsR<R> &P, const R *u)
     {
@@ -212,7 +256,8 @@ template <int DIM> struct ShallowWater {
         }
     }
 
-    template <class R> __device__ static bool eval(const ParamsR<R> &P, const Ctx<R> &cx, R t, R &B, R &dB)
+    template <class R> __device__ static bool eval(const ParamsR<R> &P, const Ctx<R> &cx, R t, R &B, R &dB,
+                                                   R *Dout = nullptr)
     {
         constexpr bool FAST = sizeof(R) == 4;
         const R gV4 = P.gV4;
@@ -294,6 +339,11 @@ template <int DIM> struct ShallowWater {
             R dot = D1 * cx.d[k][0] + bk * cx.d[k][1 + dax];
             if (DIM == 2) dot += ct * cx.d[k][2 - dax];
             dB -= dot;
+            if (Dout) {  // Delta_k = p - p'_k in the components (p_1, v_x[, v_y])
+                Dout[k * M + 0] = D1;
+                Dout[k * M + 1 + dax] = bk;
+                if (DIM == 2) Dout[k * M + 2 - dax] = ct;
+            }
         }
         return good;
     }
@@ -329,6 +379,37 @@ struct Euler2 {
         }
     }
 
+    template <class R> __device__ static void equilibrium_jacobian(const ParamsR<R> &P, const R *u, R *E)
+    {
+        const R rho = u[0], mx = u[1], my = u[2], En = u[3];
+        const R vx = mx / rho, vy = my / rho, gm = P.gamma_m1;
+        const R p = gm * (En - R(0.5) * (mx * vx + my * vy));
+        const R dp[4] = {gm * R(0.5) * (vx * vx + vy * vy), -gm * vx, -gm * vy, gm};
+        const R H = (En + p) / rho;  // total enthalpy
+        R A[2][4][4];
+        // phi^x = (m_x, m_x v_x + p, m_y v_x, v_x (E + p))
+        A[0][0][0] = R(0); A[0][0][1] = R(1); A[0][0][2] = R(0); A[0][0][3] = R(0);
+        A[0][1][0] = -vx * vx + dp[0]; A[0][1][1] = R(2) * vx + dp[1]; A[0][1][2] = dp[2]; A[0][1][3] = dp[3];
+        A[0][2][0] = -vx * vy; A[0][2][1] = vy; A[0][2][2] = vx; A[0][2][3] = R(0);
+        A[0][3][0] = -vx * H + vx * dp[0]; A[0][3][1] = H + vx * dp[1]; A[0][3][2] = vx * dp[2];
+        A[0][3][3] = vx + vx * dp[3];
+        // phi^y = (m_y, m_x v_y, m_y v_y + p, v_y (E + p))
+        A[1][0][0] = R(0); A[1][0][1] = R(0); A[1][0][2] = R(1); A[1][0][3] = R(0);
+        A[1][1][0] = -vx * vy; A[1][1][1] = vy; A[1][1][2] = vx; A[1][1][3] = R(0);
+        A[1][2][0] = -vy * vy + dp[0]; A[1][2][1] = dp[1]; A[1][2][2] = R(2) * vy + dp[2]; A[1][2][3] = dp[3];
+        A[1][3][0] = -vy * H + vy * dp[0]; A[1][3][1] = vy * dp[1]; A[1][3][2] = H + vy * dp[2];
+        A[1][3][3] = vy + vy * dp[3];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = k & 1;
+            const R s2V = (k < 2 ? R(1) : R(-1)) * P.inv2V;
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int n = 0; n < 4; ++n) E[(k * 4 + m) * 4 + n] = (m == n ? R(0.25) : R(0)) + s2V * A[j][m][n];
+        }
+    }
+
     template <class R> __device__ static bool admissible(const ParamsR<R> &P, const R *u)
     {
         const R rho = u[0];
@@ -343,7 +424,8 @@ struct Euler2 {
         R unused;
     };
     template <class R> __device__ static void prepare(const ParamsR<R> &, const R *, const R *, Ctx<R> &) {}
-    template <class R> __device__ static bool eval(const ParamsR<R> &, const Ctx<R> &, R, R &B, R &dB)
+    template <class R> __device__ static bool eval(const ParamsR<R> &, const Ctx<R> &, R, R &B, R &dB,
+                                                   R * = nullptr)
     {
         B = R(NAN);
         dB = R(NAN);

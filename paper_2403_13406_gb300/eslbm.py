@@ -26,7 +26,7 @@ EXPORTS = ("eslbm_abi_version", "eslbm_status_string", "eslbm_query", "eslbm_cre
            "eslbm_set_stream", "eslbm_last_error", "eslbm_init_equilibrium", "eslbm_init_distributions",
            "eslbm_step", "eslbm_transport", "eslbm_relax", "eslbm_read_moments", "eslbm_read_distributions",
            "eslbm_read_totals", "eslbm_get_diagnostics", "eslbm_reset_diagnostics", "eslbm_use_graph",
-           "eslbm_read_totals_noalloc")
+           "eslbm_read_totals_noalloc", "eslbm_gradient_workspace", "eslbm_gradient")
 
 
 class Config(ctypes.Structure):
@@ -84,6 +84,9 @@ def lib():
         "eslbm_reset_diagnostics": (ctypes.c_int, [H]),
         "eslbm_use_graph": (ctypes.c_int, [H, i32]),
         "eslbm_read_totals_noalloc": (ctypes.c_int, [ctypes.POINTER(Config), vp, i64, vp, i32, vp]),
+        "eslbm_gradient_workspace": (ctypes.c_int, [ctypes.POINTER(Config), i64, i64,
+                                                    ctypes.POINTER(ctypes.c_uint64)]),
+        "eslbm_gradient": (ctypes.c_int, [H, vp, vp, vp, i64, i64, vp, ctypes.c_uint64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -264,3 +267,20 @@ class Simulation:
 
     def reset_diagnostics(self):
         return self._check(lib().eslbm_reset_diagnostics(self.h))
+
+    def gradient(self, u0, dJ_duT, n, K=50):
+        """dJ/du0 (CUDA float64 tensor) for the moments after n steps from equilibrium at u0,
+        given the cotangent dJ/du_T; checkpoints every K steps (the workspace is a torch tensor)."""
+        torch = self.torch
+        nb = ctypes.c_uint64()
+        st = lib().eslbm_gradient_workspace(ctypes.byref(self.cfg), int(n), int(K), ctypes.byref(nb))
+        self._check(st)
+        ws = torch.empty(int(nb.value) + 256, dtype=torch.uint8, device=self.device)
+        ptr = (ws.data_ptr() + 255) // 256 * 256
+        shape = (self.M,) + self.grid_shape
+        u0 = u0.to(device=self.device, dtype=torch.float64).contiguous().reshape(shape)
+        g = dJ_duT.to(device=self.device, dtype=torch.float64).contiguous().reshape(shape)
+        out = torch.empty(shape, dtype=torch.float64, device=self.device)
+        self._check(lib().eslbm_gradient(self.h, u0.data_ptr(), g.data_ptr(), out.data_ptr(), int(n), int(K), ptr,
+                                         nb.value))
+        return out
