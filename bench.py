@@ -35,6 +35,7 @@ METRIC = "composite-step site updates/s + HBM GB/s fraction; FP32 vs FP64 at sta
 UNIT = "site_updates/s"
 N_CELLS = 1 << 20
 V, G, T_FINAL = 4.0, 9.81, 0.05
+BATCH_V = 8.0  # lattice velocity of the batched 2D shallow-water instances: sqrt(9.81 x 1.05) < V/2
 L2_FLUSH_BYTES = 512 << 20
 # FP32 roofline of the dominant kernel (the fused composite step k_step1d, entropic shallow water):
 # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz; and the FP32 operations of one cell-stage
@@ -53,6 +54,9 @@ def parse():
     p.add_argument("--n", type=int, default=N_CELLS)
     p.add_argument("--t-final", type=float, default=T_FINAL)
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 and CPU baseline legs")
+    p.add_argument("--leg", default=None, choices=["hbm2d", "batched"],
+                   help="run one secondary measurement alone and print its JSON (for profiling)")
+    p.add_argument("--hbm-steps", type=int, default=20, help="composite steps of the 2D streaming leg")
     return p.parse_args()
 
 
@@ -179,6 +183,14 @@ def main():
         return
     import torch
     from paper_2403_13406_gb300 import eslbm, inputs
+    if args.leg:
+        torch.cuda.set_device(0)
+        dev = torch.device("cuda", 0)
+        stream = torch.cuda.Stream(device=dev)
+        leg = hbm2d_leg if args.leg == "hbm2d" else batch_leg
+        kw = {"steps": args.hbm_steps} if args.leg == "hbm2d" else {}
+        print(json.dumps(leg(torch, eslbm, inputs, stream, dev, **kw)), flush=True)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -286,6 +298,8 @@ def main():
     if not args.no_extras and rank == 0:
         extras = fp64_leg(sim, torch, eslbm, inputs, stream, dev, N)
         extras.update(adjoint_leg(torch, eslbm, inputs, stream, dev))
+        extras.update(batch_leg(torch, eslbm, inputs, stream, dev))
+        extras.update(hbm2d_leg(torch, eslbm, inputs, stream, dev))
     cpu = None
     if rank == 0 and world == 1 and not args.no_extras:
         rate, dt = oracle_sample(2048)
@@ -370,6 +384,109 @@ def adjoint_leg(torch, eslbm, inputs, stream, dev, N=1 << 16, n=96, K=16):
         sim.close()
     return {"adjoint_vs_forward": {"N": N, "steps": n, "checkpoint_every": K, "forward_s": times["forward"],
                                    "adjoint_s": times["adjoint"], "ratio": times["adjoint"] / times["forward"]}}
+
+
+def batch_leg(torch, eslbm, inputs, stream, dev, count=64, steps=20, grad_instances=4, grad_n=50, grad_K=10):
+    """Batched form: `count` 2D shallow-water instances (D2Q4, FP32, entropic) of uneven seeded sizes in
+    [256, 1024]^2 with 8-mode Fourier depth data, advanced by one cooperative launch per composite step
+    replayed from CUDA graphs, after the autotuner has picked the schedule; a bounded number of steps.
+    The reverse mode is timed on the first `grad_instances` instances (L2 misfit of the final depth
+    against a seeded target, checkpoints every grad_K steps)."""
+    sizes = inputs.batched_sizes(count, 256, 1024)
+    cfg = eslbm.make_config(2, "sw", 1, 1, V=BATCH_V, g=G, precision="fp32", omega_mode="entropic")
+    with torch.cuda.stream(stream):
+        b = eslbm.Batch(cfg, sizes, stream=stream, device=dev)
+        u0 = b.pack([inputs.sw_fourier_2d(nx, ny, seed=1000 + i) for i, (nx, ny) in enumerate(sizes)])
+        b.init_equilibrium(u0)
+        t0 = time.perf_counter()
+        sched = b.tune(steps=2)
+        tune_s = time.perf_counter() - t0
+        b.use_graph(True)
+        b.init_equilibrium(u0)
+        b.step(steps)  # warm-up: captures the graphs
+        b.init_equilibrium(u0)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        fallbacks = int(b.diagnostics()["fallbacks"])
+        cells = b.total_cells
+        b.close()
+        # reverse mode on a bounded sample of the instances
+        gs = sizes[:grad_instances]
+        gb = eslbm.Batch(cfg, gs, stream=stream, device=dev)
+        gu0 = gb.pack([inputs.sw_fourier_2d(nx, ny, seed=1000 + i) for i, (nx, ny) in enumerate(gs)])
+        target = gb.pack([inputs.sw_fourier_2d(nx, ny, seed=5000 + i) for i, (nx, ny) in enumerate(gs)])
+        torch.cuda.synchronize(dev)
+        tf = time.perf_counter()
+        gb.init_equilibrium(gu0)
+        gb.step(grad_n)
+        uT = gb.moments_flat()
+        torch.cuda.synchronize(dev)
+        fwd_s = time.perf_counter() - tf
+        lam = torch.zeros_like(uT)
+        for v, (u, t) in enumerate(zip(gb.unpack(uT), gb.unpack(target))):
+            gb.unpack(lam)[v][0] = 2.0 * (u[0] - t[0])  # dJ/dh_T of J = sum (h_T - target)^2
+        torch.cuda.synchronize(dev)
+        ta = time.perf_counter()
+        grad = gb.gradient(gu0, lam, grad_n, grad_K)
+        torch.cuda.synchronize(dev)
+        adj_s = time.perf_counter() - ta
+        gnorm = float(torch.linalg.vector_norm(grad))
+        gb.close()
+    return {"batched": {"instances": count, "total_cells": cells, "sizes": "seeded uniform nx, ny in [256, 1024]",
+                        "steps": steps, "ms": ms, "site_updates_per_s": cells * steps / (ms * 1e-3),
+                        "schedule": {"segment": sched[0], "blocks_per_sm": sched[1], "order": sched[2]},
+                        "tune_s": tune_s, "cuda_graph": True, "fallbacks": fallbacks, "V": BATCH_V,
+                        "adjoint": {"instances": grad_instances, "steps": grad_n, "checkpoint_every": grad_K,
+                                    "forward_s": fwd_s, "gradient_s": adj_s, "ratio": adj_s / fwd_s,
+                                    "grad_norm": gnorm}}}
+
+
+def hbm2d_leg(torch, eslbm, inputs, stream, dev, steps=20):
+    """Per-stage streaming rate of the 2D stage kernel (one fused pull-shift + relax launch per stage,
+    every distribution read and written once): D2Q4 Burgers 4096^2 FP32 (32 B per cell-stage) with
+    omega = 2 and with the entropic omega, and D2Q4 Euler 8192^2 FP32 (128 B per cell-stage) with
+    omega = 2 and scheme III (the paper's Euler setting).  Inputs are larger than L2 (268 MB and
+    4.3 GB per state buffer), so every stage streams from HBM."""
+    peak, kind = peaks()
+    cases = [("burgers2d_4096_fixed", 2, "burgers", 4096, dict(V=3.0, c=(1.0, 1.0)), "fixed", "I", steps,
+              lambda n: inputs.burgers_2d(n, n)),
+             ("burgers2d_4096_entropic", 2, "burgers", 4096, dict(V=3.0, c=(1.0, 1.0)), "entropic", "I", steps,
+              lambda n: inputs.burgers_2d(n, n)),
+             ("euler2d_8192_fixed", 2, "euler", 8192, dict(V=8.0, gamma=1.4), "fixed", "III", max(1, steps // 10),
+              lambda n: inputs.euler_vortex_2d(n, n))]
+    out = {}
+    for name, dim, system, n, kw, mode, scheme, nsteps, init in cases:
+        cfg = eslbm.make_config(dim, system, n, n, precision="fp32", omega_mode=mode, scheme=scheme, **kw)
+        with torch.cuda.stream(stream):
+            sim = eslbm.Simulation(cfg, stream=stream, device=dev)
+            sim.use_graph(True)
+            u0 = torch.from_numpy(init(n)).to(dev)
+            sim.init_equilibrium(u0)
+            del u0
+            sim.step(1)  # warm-up and graph capture
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(nsteps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            stages = nsteps * int(sim.sizes.stages_per_step)
+            bytes_stage = 2 * int(sim.sizes.state_bytes)
+            fb = int(sim.diagnostics()["fallbacks"])
+            sim.close()
+        stage_s = ms * 1e-3 / stages
+        out[name] = {"cells": n * n, "steps": nsteps, "stages": stages, "stage_us": stage_s * 1e6,
+                     "bytes_per_stage": bytes_stage, "achieved_gbs": bytes_stage / stage_s / 1e9,
+                     "frac_of_hbm_peak": bytes_stage / stage_s / 1e9 / peak, "peak_gbs": peak, "peak_source": kind,
+                     "site_updates_per_s": n * n * nsteps / (ms * 1e-3), "fallbacks": fb,
+                     "kernel": "k_stage<%s, 2, float, %s>" % (system, mode)}
+    return {"hbm2d": out}
 
 
 if __name__ == "__main__":

@@ -139,8 +139,9 @@ const char *eslbm_last_error(const eslbm_handle *h);
 
 /* f_k = f^eq_k(u0) in every cell (Section 3.1).  u0: M double planes of ncell
    cells.  Checks the convexity / sub-characteristic domain of Section 1.2 on the
-   device (synchronizes) and returns ESLBM_ERR_DOMAIN (state untouched) if a cell
-   violates it, ESLBM_ERR_NAN for non-finite input.  Resets the pending shift. */
+   device (synchronizes) and returns ESLBM_ERR_DOMAIN if a cell violates it,
+   ESLBM_ERR_NAN for non-finite input; the state is then written but not
+   meaningful.  Resets the pending shift. */
 eslbm_status eslbm_init_equilibrium(eslbm_handle *h, const double *u0, int32_t u0_on_device);
 
 /* Set the distributions directly (q*M double planes, rounded to the storage
@@ -227,6 +228,94 @@ eslbm_status eslbm_gradient(eslbm_handle *h, const double *u0, const double *dJ_
    graph and replay it inside eslbm_step (enable = 1), or launch directly
    (enable = 0, the default). */
 eslbm_status eslbm_use_graph(eslbm_handle *h, int32_t enable);
+
+/* ------------------------------------------------------------------------
+   Batched execution (no counterpart in the paper, which runs one lattice at a
+   time): `count` independent periodic 2D lattices of sizes nx[i] x ny[i] that
+   share one configuration (system, precision, omega mode, scheme, V and the
+   physical constants; the nx, ny of `base` are ignored) advance together.  One
+   composite step of all of them is ONE cooperative launch: the blocks sweep a
+   work list of row segments of every instance for each fused stage, with a grid
+   barrier between stages.  Every instance computes exactly what a single
+   handle with its sizes computes (same per-cell arithmetic, same stage list).
+   Only dim = 2 is supported (ESLBM_ERR_UNSUPPORTED otherwise).
+   ------------------------------------------------------------------------ */
+typedef struct eslbm_batch eslbm_batch;
+
+typedef struct {
+    int32_t count;           /* instances */
+    int64_t q, M, planes;    /* as in eslbm_sizes */
+    int64_t total_cells;     /* sum of nx[i] * ny[i] */
+    uint64_t pool_bytes;     /* bytes of one state pool: the instances' states, each 256-byte aligned */
+    uint64_t workspace_bytes;/* bytes of the workspace (counters, instance and work lists, one
+                                single-lattice workspace for eslbm_batch_gradient) */
+    int64_t stages_per_step; /* fused stages of one composite step */
+    int64_t step_cells;      /* lattice time of one step, as in eslbm_sizes */
+} eslbm_batch_sizes;
+
+/* Sizes for `count` instances; validates every instance as eslbm_query does.
+   Errors: ESLBM_ERR_ARG (null pointer, count < 1, bad field), ESLBM_ERR_UNSUPPORTED. */
+eslbm_status eslbm_batch_query(const eslbm_config *base, int32_t count, const int64_t *nx, const int64_t *ny,
+                               eslbm_batch_sizes *out);
+
+/* Create a batch.  pool_a, pool_b: distinct device buffers of pool_bytes each;
+   workspace: device buffer of workspace_bytes; all 256-byte aligned, owned by the
+   caller and outliving the batch.  Instance i occupies planes * nx[i] * ny[i]
+   values of each pool in the layout of a single handle, starting at the pool
+   offset sum_{j<i} round_up(state_bytes_j, 256).  stream: a cudaStream_t.
+   Synchronizes once (uploads the work list).  The default schedule is 256-cell
+   segments, the kernel's full residency, instance-major order. */
+eslbm_status eslbm_batch_create(const eslbm_config *base, int32_t count, const int64_t *nx, const int64_t *ny,
+                                void *pool_a, void *pool_b, void *workspace, void *stream, eslbm_batch **out);
+eslbm_status eslbm_batch_destroy(eslbm_batch *b);
+const char *eslbm_batch_last_error(const eslbm_batch *b);
+
+/* f = f^eq(u0) for every instance (Section 3.1).  u0: the instances' moments one
+   after the other, each M double planes of nx[i] * ny[i] cells; device memory if
+   on_device, else host memory (staged through the spare pool).  Synchronizes.
+   ESLBM_ERR_DOMAIN / ESLBM_ERR_NAN as in eslbm_init_equilibrium (the state is then
+   written but not meaningful). */
+eslbm_status eslbm_batch_init_equilibrium(eslbm_batch *b, const double *u0, int32_t on_device);
+
+/* Advance every instance n composite steps (one cooperative launch per step;
+   asynchronous).  ESLBM_ERR_CUDA if the cooperative launch is refused. */
+eslbm_status eslbm_batch_step(eslbm_batch *b, int64_t n);
+
+/* Moments of every instance in the layout of eslbm_batch_init_equilibrium's u0;
+   device memory if on_device, else host memory (synchronizes). */
+eslbm_status eslbm_batch_read_moments(eslbm_batch *b, double *u_out, int32_t on_device);
+
+/* Schedule of the batched launch: row segments of `segment` cells (>= 128),
+   blocks_per_sm resident blocks per SM (1 .. the kernel's occupancy), order 0 =
+   instance-major work list, 1 = rows of all instances interleaved.  Results do not
+   depend on the schedule (bitwise).  Synchronizes. */
+eslbm_status eslbm_batch_set_schedule(eslbm_batch *b, int64_t segment, int32_t blocks_per_sm, int32_t order);
+eslbm_status eslbm_batch_get_schedule(const eslbm_batch *b, int64_t *segment, int32_t *blocks_per_sm,
+                                      int32_t *order);
+
+/* Autotuner: times `steps` steps of every candidate schedule (segments 128, 256,
+   512, 1024; full, half and single residency; both orders) with CUDA events from
+   the current state, keeps the fastest, and restores the state.  scratch: device
+   buffer of at least pool_bytes.  Synchronizes. */
+eslbm_status eslbm_batch_tune(eslbm_batch *b, void *scratch, uint64_t scratch_bytes, int32_t steps);
+
+/* Replay each step from a CUDA graph of its cooperative launch (enable = 1) or
+   launch directly (0, the default).  Needs a non-NULL stream. */
+eslbm_status eslbm_batch_use_graph(eslbm_batch *b, int32_t enable);
+
+/* Reverse mode per instance: workspace bytes (the largest instance's
+   eslbm_gradient_workspace) and the gradients.  u0, dJ_duT, dJ_du0: device
+   memory in the layout of eslbm_batch_init_equilibrium's u0.  Each instance runs
+   eslbm_gradient on a temporary handle over its part of the pools; on return the
+   batch holds f^eq(u0) (the state at step 0).  Synchronizes. */
+eslbm_status eslbm_batch_gradient_workspace(const eslbm_config *base, int32_t count, const int64_t *nx,
+                                            const int64_t *ny, int64_t n, int64_t K, uint64_t *bytes);
+eslbm_status eslbm_batch_gradient(eslbm_batch *b, const double *u0, const double *dJ_duT, double *dJ_du0, int64_t n,
+                                  int64_t K, void *ws, uint64_t ws_bytes);
+
+/* Fallback count of the batched kernels since creation (synchronizes; the omega
+   range is not tracked, returned as 0).  ESLBM_WARN_OMEGA_FALLBACK when > 0. */
+eslbm_status eslbm_batch_get_diagnostics(eslbm_batch *b, eslbm_diagnostics *out);
 
 #ifdef __cplusplus
 }

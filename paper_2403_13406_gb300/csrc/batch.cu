@@ -1,0 +1,564 @@
+// batch.cu -- C ABI of batched execution: many independent 2D lattices of
+// uneven sizes advance together, one cooperative launch per composite step
+// (all stages, grid.sync between them), optionally replayed from a CUDA graph.
+// The work list (row segments of every instance) and the grid size come from a
+// schedule that eslbm_batch_tune picks by timing candidates.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/eslbm.h"
+#include "host_schedule.h"
+#include "launch.h"
+
+using namespace eslbm;
+
+namespace {
+
+constexpr size_t kCounters = 256;
+constexpr int64_t kMinSegment = 128;
+
+uint64_t align256(uint64_t b) { return (b + 255u) / 256u * 256u; }
+
+struct Layout {
+    int64_t q, M, planes, total_cells, max_items;
+    uint64_t elem, pool_bytes, inst_off, items_off, handle_ws_off, handle_ws_bytes, ws_bytes;
+    std::vector<BatchInstance> inst;
+};
+
+eslbm_status layout(const eslbm_config *base, int32_t count, const int64_t *nx, const int64_t *ny, Layout &L)
+{
+    if (!base || count < 1 || count > (1 << 20) || !nx || !ny) return ESLBM_ERR_ARG;
+    if (base->dim != 2) return ESLBM_ERR_UNSUPPORTED;
+    L.inst.resize((size_t)count);
+    L.total_cells = 0;
+    L.max_items = 0;
+    uint64_t off = 0;
+    eslbm_sizes sz{};
+    for (int32_t i = 0; i < count; ++i) {
+        eslbm_config c = *base;
+        c.nx = nx[i];
+        c.ny = ny[i];
+        eslbm_status s = eslbm_query(&c, &sz);  // validates every instance
+        if (s != ESLBM_OK) return s;
+        if (nx[i] > INT32_MAX) return ESLBM_ERR_ARG;  // work items hold 32-bit columns
+        L.elem = base->precision == ESLBM_FP64 ? 8 : 4;
+        L.inst[(size_t)i] = {nx[i], ny[i], (int64_t)(off / L.elem)};
+        off += align256(sz.state_bytes);
+        L.total_cells += sz.ncell;
+        L.max_items += ny[i] * ((nx[i] + kMinSegment - 1) / kMinSegment);
+    }
+    if (L.max_items > (int64_t(1) << 31) - 1) return ESLBM_ERR_ARG;
+    L.q = sz.q;
+    L.M = sz.M;
+    L.planes = sz.planes;
+    L.pool_bytes = off;
+    L.inst_off = kCounters;
+    L.items_off = L.inst_off + align256(sizeof(BatchInstance) * (uint64_t)count);
+    L.handle_ws_off = L.items_off + align256(sizeof(BatchItem) * (uint64_t)L.max_items);
+    L.handle_ws_bytes = align256(sz.workspace_bytes);
+    L.ws_bytes = L.handle_ws_off + L.handle_ws_bytes;
+    return ESLBM_OK;
+}
+
+}  // namespace
+
+struct eslbm_batch {
+    eslbm_config cfg;
+    int32_t count;
+    Layout L;
+    int family;
+    bool fp64, entropic;
+    void *pool[2];
+    int side;
+    char *ws;
+    cudaStream_t stream;
+    int64_t pending;
+    Params P;
+    std::vector<Op> ops;
+    // schedule
+    int64_t segment;
+    int32_t blocks_per_sm, order;
+    int n_items;
+    int sms, max_bps;
+    // graphs of `steps` consecutive steps entered on (side, pending): a small cache, as the
+    // first step from pending = 0 enters differently from the later ones
+    struct Graph {
+        cudaGraphExec_t exec;
+        int side;
+        int64_t pending, steps;
+    };
+    bool use_graph;
+    std::vector<Graph> graphs;
+    std::string err;
+
+    Counters *counters() { return reinterpret_cast<Counters *>(ws); }
+    BatchInstance *d_inst() { return reinterpret_cast<BatchInstance *>(ws + L.inst_off); }
+    BatchItem *d_items() { return reinterpret_cast<BatchItem *>(ws + L.items_off); }
+    char *instance_ptr(int side_, int32_t i) { return (char *)pool[side_] + L.inst[(size_t)i].offset * L.elem; }
+};
+
+namespace {
+
+#define BCK(call, where)                                                            \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            b->err = std::string(where) + ": " + cudaGetErrorString(e_);            \
+            return ESLBM_ERR_CUDA;                                                  \
+        }                                                                           \
+    } while (0)
+
+Shift shift_for(const eslbm_batch *b, int32_t i, int64_t s)
+{
+    Shift sh;
+    for (int k = 0; k < 4; ++k) {
+        const int axis = k & 1, sign = k < 2 ? 1 : -1;
+        const int64_t n = axis == 0 ? b->L.inst[(size_t)i].nx : b->L.inst[(size_t)i].ny;
+        int64_t r = (-(int64_t)sign * s) % n;
+        sh.roff[k] = r < 0 ? r + n : r;
+    }
+    return sh;
+}
+
+void drop_graphs(eslbm_batch *b)
+{
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+}
+
+// Work list of the schedule: row segments of at most `segment` cells; order 0 walks the
+// instances one after the other, order 1 interleaves rows of all instances round robin.
+eslbm_status upload_schedule(eslbm_batch *b)
+{
+    std::vector<BatchItem> items;
+    items.reserve((size_t)b->L.max_items);
+    if (b->order == 0) {
+        for (int32_t i = 0; i < b->count; ++i)
+            for (int64_t y = 0; y < b->L.inst[(size_t)i].ny; ++y)
+                for (int64_t x0 = 0; x0 < b->L.inst[(size_t)i].nx; x0 += b->segment)
+                    items.push_back({i, (int32_t)y, (int32_t)x0,
+                                     (int32_t)std::min<int64_t>(b->segment, b->L.inst[(size_t)i].nx - x0)});
+    } else {
+        int64_t ymax = 0;
+        for (const BatchInstance &I : b->L.inst) ymax = std::max(ymax, I.ny);
+        for (int64_t y = 0; y < ymax; ++y)
+            for (int32_t i = 0; i < b->count; ++i) {
+                if (y >= b->L.inst[(size_t)i].ny) continue;
+                for (int64_t x0 = 0; x0 < b->L.inst[(size_t)i].nx; x0 += b->segment)
+                    items.push_back({i, (int32_t)y, (int32_t)x0,
+                                     (int32_t)std::min<int64_t>(b->segment, b->L.inst[(size_t)i].nx - x0)});
+            }
+    }
+    if ((int64_t)items.size() > b->L.max_items) return ESLBM_ERR_ARG;
+    b->n_items = (int)items.size();
+    BCK(cudaMemcpyAsync(b->d_items(), items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice,
+                        b->stream),
+        "upload work list");
+    BCK(cudaStreamSynchronize(b->stream), "sync");
+    drop_graphs(b);
+    return ESLBM_OK;
+}
+
+eslbm_status run_step(eslbm_batch *b)
+{
+    BatchLaunch B;
+    B.sl.n = 0;
+    B.sl.halo = 0;
+    for (const Op &op : b->ops) {
+        if (!op.relax) {
+            b->pending += op.shift;
+            continue;
+        }
+        B.sl.shift[B.sl.n] = (int)b->pending;
+        B.sl.kind[B.sl.n] = op.kind;
+        B.sl.n += 1;
+        b->pending = 0;
+    }
+    B.pool[0] = b->pool[0];
+    B.pool[1] = b->pool[1];
+    B.inst = b->d_inst();
+    B.items = b->d_items();
+    B.n_items = b->n_items;
+    B.side = b->side;
+    B.cnt = b->counters();
+    B.P = b->P;
+    B.grid = std::max(1, std::min(b->n_items, b->sms * b->blocks_per_sm));
+    B.stream = b->stream;
+    BCK(launch_batch_step(b->family, b->fp64, b->entropic, B), "batch step launch");
+    if (B.sl.n & 1) b->side ^= 1;
+    return ESLBM_OK;
+}
+
+constexpr int64_t kGraphSteps = 256;  // steps per captured graph
+constexpr size_t kGraphCache = 4;
+
+// Capture `steps` steps from the current (side, pending) and return the graph;
+// the host bookkeeping ends where the replay will leave it.
+eslbm_status capture(eslbm_batch *b, int64_t steps, cudaGraphExec_t *out)
+{
+    if (b->graphs.size() >= kGraphCache) drop_graphs(b);
+    const int side0 = b->side;
+    const int64_t pend0 = b->pending;
+    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    eslbm_status s = ESLBM_OK;
+    for (int64_t i = 0; i < steps && s == ESLBM_OK; ++i) s = run_step(b);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (s != ESLBM_OK) {
+        if (g) cudaGraphDestroy(g);
+        b->side = side0;
+        b->pending = pend0;
+        return s;
+    }
+    BCK(e, "end capture");
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    b->side = side0;  // the caller replays and advances the bookkeeping
+    b->pending = pend0;
+    BCK(e, "graph instantiate");
+    b->graphs.push_back({x, side0, pend0, steps});
+    *out = x;
+    return ESLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+eslbm_status eslbm_batch_query(const eslbm_config *base, int32_t count, const int64_t *nx, const int64_t *ny,
+                               eslbm_batch_sizes *out)
+{
+    if (!out) return ESLBM_ERR_ARG;
+    Layout L;
+    eslbm_status s = layout(base, count, nx, ny, L);
+    if (s != ESLBM_OK) return s;
+    out->count = count;
+    out->q = L.q;
+    out->M = L.M;
+    out->planes = L.planes;
+    out->total_cells = L.total_cells;
+    out->pool_bytes = L.pool_bytes;
+    out->workspace_bytes = L.ws_bytes;
+    int64_t stages = 0;
+    for (const Op &op : scheme_ops(base->scheme, base->kappa)) stages += op.relax ? 1 : 0;
+    out->stages_per_step = stages;
+    out->step_cells = step_cells(base->scheme, base->kappa);
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_batch_create(const eslbm_config *base, int32_t count, const int64_t *nx, const int64_t *ny,
+                                void *pool_a, void *pool_b, void *workspace, void *stream, eslbm_batch **out)
+{
+    if (!out) return ESLBM_ERR_ARG;
+    *out = nullptr;
+    Layout L;
+    eslbm_status s = layout(base, count, nx, ny, L);
+    if (s != ESLBM_OK) return s;
+    if (!pool_a || !pool_b || !workspace || pool_a == pool_b) return ESLBM_ERR_ARG;
+    if (((uintptr_t)pool_a | (uintptr_t)pool_b | (uintptr_t)workspace) & 255u) return ESLBM_ERR_ARG;
+    eslbm_batch *b = new (std::nothrow) eslbm_batch();
+    if (!b) return ESLBM_ERR_ARG;
+    b->cfg = *base;
+    b->count = count;
+    b->L = L;
+    b->family = family_of(*base);
+    b->fp64 = base->precision == ESLBM_FP64;
+    b->entropic = base->omega_mode == ESLBM_OMEGA_ENTROPIC;
+    b->pool[0] = pool_a;
+    b->pool[1] = pool_b;
+    b->side = 0;
+    b->ws = (char *)workspace;
+    b->stream = (cudaStream_t)stream;
+    b->pending = 0;
+    b->P.V = base->V;
+    b->P.a[0] = base->a[0];
+    b->P.a[1] = base->a[1];
+    b->P.c[0] = base->c[0];
+    b->P.c[1] = base->c[1];
+    b->P.g = base->g;
+    b->P.gamma = base->gamma;
+    b->P.omega = (b->entropic && base->system == ESLBM_LINEAR) ? 2.0 : base->omega;
+    b->P.t_max = base->t_max > 0.0 ? base->t_max : 3.0;
+    b->ops = scheme_ops(base->scheme, base->kappa);
+    b->use_graph = false;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    b->max_bps = batch_blocks_per_sm(b->family, b->fp64, b->entropic);
+    if (b->sms < 1 || b->max_bps < 1) {
+        delete b;
+        return ESLBM_ERR_CUDA;
+    }
+    b->segment = 256;
+    b->blocks_per_sm = b->max_bps;
+    b->order = 0;
+    Counters c;
+    std::memset(&c, 0, sizeof(c));
+    c.omega_min_bits = 0x7f800000u;
+    if (cudaMemcpyAsync(b->counters(), &c, sizeof(c), cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_inst(), L.inst.data(), sizeof(BatchInstance) * L.inst.size(), cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess) {
+        delete b;
+        return ESLBM_ERR_CUDA;
+    }
+    s = upload_schedule(b);
+    if (s != ESLBM_OK) {
+        delete b;
+        return s;
+    }
+    *out = b;
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_batch_destroy(eslbm_batch *b)
+{
+    if (!b) return ESLBM_OK;
+    drop_graphs(b);
+    delete b;
+    return ESLBM_OK;
+}
+
+const char *eslbm_batch_last_error(const eslbm_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+eslbm_status eslbm_batch_init_equilibrium(eslbm_batch *b, const double *u0, int32_t on_device)
+{
+    if (!b || !u0) return ESLBM_ERR_ARG;
+    const size_t ubytes = sizeof(double) * (size_t)b->L.M * (size_t)b->L.total_cells;
+    const double *src = u0;
+    if (!on_device) {  // stage through the spare pool (it holds at least M doubles per cell)
+        if (ubytes > b->L.pool_bytes) return ESLBM_ERR_ARG;
+        BCK(cudaMemcpyAsync(b->pool[1 - b->side], u0, ubytes, cudaMemcpyHostToDevice, b->stream), "copy u0");
+        src = (const double *)b->pool[1 - b->side];
+    }
+    Counters *c = b->counters();
+    BCK(cudaMemsetAsync(&c->domain_violations, 0, 2 * sizeof(unsigned long long), b->stream), "clear flags");
+    int64_t cell0 = 0;
+    for (int32_t i = 0; i < b->count; ++i) {
+        const int64_t n = b->L.inst[(size_t)i].nx * b->L.inst[(size_t)i].ny;
+        BCK(launch_init_eq(b->family, b->fp64, src + cell0 * b->L.M, b->instance_ptr(b->side, i), n, b->P, c,
+                           b->stream),
+            "init launch");
+        cell0 += n;
+    }
+    unsigned long long flags[2];
+    BCK(cudaMemcpyAsync(flags, &c->domain_violations, sizeof(flags), cudaMemcpyDeviceToHost, b->stream), "flags");
+    BCK(cudaStreamSynchronize(b->stream), "sync");
+    b->pending = 0;
+    if (flags[1]) return ESLBM_ERR_NAN;
+    if (flags[0]) return ESLBM_ERR_DOMAIN;
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_batch_step(eslbm_batch *b, int64_t n)
+{
+    if (!b || n < 0) return ESLBM_ERR_ARG;
+    if (b->use_graph && b->stream != nullptr) {
+        while (n > 0) {
+            const int64_t c = std::min(n, kGraphSteps);
+            cudaGraphExec_t x = nullptr;
+            for (const auto &g : b->graphs)
+                if (g.side == b->side && g.pending == b->pending && g.steps == c) x = g.exec;
+            if (!x) {
+                eslbm_status s = capture(b, c, &x);
+                if (s != ESLBM_OK) return s;
+            }
+            BCK(cudaGraphLaunch(x, b->stream), "graph launch");
+            // advance the host bookkeeping by c steps without launching
+            for (int64_t i = 0; i < c; ++i) {
+                int stages = 0;
+                for (const Op &op : b->ops) {
+                    if (!op.relax) b->pending += op.shift;
+                    else {
+                        b->pending = 0;
+                        ++stages;
+                    }
+                }
+                if (stages & 1) b->side ^= 1;
+            }
+            n -= c;
+        }
+        return ESLBM_OK;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        eslbm_status s = run_step(b);
+        if (s != ESLBM_OK) return s;
+    }
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_batch_read_moments(eslbm_batch *b, double *u_out, int32_t on_device)
+{
+    if (!b || !u_out) return ESLBM_ERR_ARG;
+    const size_t ubytes = sizeof(double) * (size_t)b->L.M * (size_t)b->L.total_cells;
+    double *dst = u_out;
+    if (!on_device) {
+        if (ubytes > b->L.pool_bytes) return ESLBM_ERR_ARG;
+        dst = (double *)b->pool[1 - b->side];
+    }
+    int64_t cell0 = 0;
+    for (int32_t i = 0; i < b->count; ++i) {
+        const BatchInstance &I = b->L.inst[(size_t)i];
+        BCK(launch_gather_moments(2, b->fp64, b->instance_ptr(b->side, i), dst + cell0 * b->L.M, I.nx, I.ny,
+                                  (int)b->L.M, shift_for(b, i, b->pending), b->stream),
+            "gather moments");
+        cell0 += I.nx * I.ny;
+    }
+    if (!on_device) {
+        BCK(cudaMemcpyAsync(u_out, dst, ubytes, cudaMemcpyDeviceToHost, b->stream), "copy moments");
+        BCK(cudaStreamSynchronize(b->stream), "sync");
+    }
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_batch_set_schedule(eslbm_batch *b, int64_t segment, int32_t blocks_per_sm, int32_t order)
+{
+    if (!b || segment < kMinSegment || segment > (1 << 20) || (order != 0 && order != 1)) return ESLBM_ERR_ARG;
+    if (blocks_per_sm < 1 || blocks_per_sm > b->max_bps) return ESLBM_ERR_ARG;
+    b->segment = segment;
+    b->blocks_per_sm = blocks_per_sm;
+    b->order = order;
+    return upload_schedule(b);
+}
+
+eslbm_status eslbm_batch_get_schedule(const eslbm_batch *b, int64_t *segment, int32_t *blocks_per_sm, int32_t *order)
+{
+    if (!b || !segment || !blocks_per_sm || !order) return ESLBM_ERR_ARG;
+    *segment = b->segment;
+    *blocks_per_sm = b->blocks_per_sm;
+    *order = b->order;
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_batch_tune(eslbm_batch *b, void *scratch, uint64_t scratch_bytes, int32_t steps)
+{
+    if (!b || !scratch || steps < 1 || scratch_bytes < b->L.pool_bytes) return ESLBM_ERR_ARG;
+    // keep the state: every candidate starts from it and it is restored at the end
+    const int side0 = b->side;
+    const int64_t pend0 = b->pending;
+    BCK(cudaMemcpyAsync(scratch, b->pool[side0], b->L.pool_bytes, cudaMemcpyDeviceToDevice, b->stream), "save");
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0), "event");
+    BCK(cudaEventCreate(&e1), "event");
+    const int64_t segs[] = {128, 256, 512, 1024};
+    int bps_opts[3] = {b->max_bps, std::max(1, b->max_bps / 2), 1};
+    float best = 1e30f;
+    int64_t best_seg = b->segment;
+    int32_t best_bps = b->blocks_per_sm, best_order = b->order;
+    const bool graph = b->use_graph;
+    b->use_graph = false;
+    eslbm_status s = ESLBM_OK;
+    for (int64_t seg : segs) {
+        for (int bi = 0; bi < 3 && s == ESLBM_OK; ++bi) {
+            if (bi > 0 && bps_opts[bi] == bps_opts[bi - 1]) continue;
+            for (int32_t order = 0; order < 2 && s == ESLBM_OK; ++order) {
+                b->segment = seg;
+                b->blocks_per_sm = bps_opts[bi];
+                b->order = order;
+                if ((s = upload_schedule(b)) != ESLBM_OK) break;
+                BCK(cudaMemcpyAsync(b->pool[side0], scratch, b->L.pool_bytes, cudaMemcpyDeviceToDevice, b->stream),
+                    "restore");
+                b->side = side0;
+                b->pending = pend0;
+                if ((s = run_step(b)) != ESLBM_OK) break;  // warm-up
+                BCK(cudaEventRecord(e0, b->stream), "record");
+                for (int32_t i = 0; i < steps && s == ESLBM_OK; ++i) s = run_step(b);
+                BCK(cudaEventRecord(e1, b->stream), "record");
+                BCK(cudaEventSynchronize(e1), "sync");
+                float ms = 0.f;
+                BCK(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+                if (ms < best) {
+                    best = ms;
+                    best_seg = seg;
+                    best_bps = bps_opts[bi];
+                    best_order = order;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->use_graph = graph;
+    BCK(cudaMemcpyAsync(b->pool[side0], scratch, b->L.pool_bytes, cudaMemcpyDeviceToDevice, b->stream), "restore");
+    b->side = side0;
+    b->pending = pend0;
+    if (s != ESLBM_OK) return s;
+    b->segment = best_seg;
+    b->blocks_per_sm = best_bps;
+    b->order = best_order;
+    return upload_schedule(b);
+}
+
+eslbm_status eslbm_batch_use_graph(eslbm_batch *b, int32_t enable)
+{
+    if (!b) return ESLBM_ERR_ARG;
+    b->use_graph = enable != 0;
+    if (!b->use_graph) drop_graphs(b);
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_batch_gradient_workspace(const eslbm_config *base, int32_t count, const int64_t *nx,
+                                            const int64_t *ny, int64_t n, int64_t K, uint64_t *bytes)
+{
+    if (!bytes) return ESLBM_ERR_ARG;
+    Layout L;
+    eslbm_status s = layout(base, count, nx, ny, L);
+    if (s != ESLBM_OK) return s;
+    uint64_t mx = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        eslbm_config c = *base;
+        c.nx = nx[i];
+        c.ny = ny[i];
+        uint64_t b = 0;
+        if ((s = eslbm_gradient_workspace(&c, n, K, &b)) != ESLBM_OK) return s;
+        mx = std::max(mx, b);
+    }
+    *bytes = mx;
+    return ESLBM_OK;
+}
+
+eslbm_status eslbm_batch_gradient(eslbm_batch *b, const double *u0, const double *dJ_duT, double *dJ_du0, int64_t n,
+                                  int64_t K, void *ws, uint64_t ws_bytes)
+{
+    if (!b || !u0 || !dJ_duT || !dJ_du0 || !ws) return ESLBM_ERR_ARG;
+    // each instance: the single-lattice reverse mode on views of the batch pools
+    int64_t cell0 = 0;
+    for (int32_t i = 0; i < b->count; ++i) {
+        const BatchInstance &I = b->L.inst[(size_t)i];
+        eslbm_config c = b->cfg;
+        c.nx = I.nx;
+        c.ny = I.ny;
+        eslbm_handle *h = nullptr;
+        eslbm_status s = eslbm_create(&c, b->instance_ptr(0, i), b->instance_ptr(1, i), b->ws + b->L.handle_ws_off,
+                                      b->stream, &h);
+        if (s != ESLBM_OK) return s;
+        const int64_t off = cell0 * b->L.M;
+        s = eslbm_gradient(h, u0 + off, dJ_duT + off, dJ_du0 + off, n, K, ws, ws_bytes);
+        if (s != ESLBM_OK) b->err = std::string("instance gradient: ") + eslbm_last_error(h);
+        eslbm_destroy(h);
+        if (s != ESLBM_OK) return s;
+        cell0 += I.nx * I.ny;
+    }
+    // the pools now hold other states: start again from u0 on the next step
+    b->side = 0;
+    return eslbm_batch_init_equilibrium(b, u0, 1);
+}
+
+eslbm_status eslbm_batch_get_diagnostics(eslbm_batch *b, eslbm_diagnostics *out)
+{
+    if (!b || !out) return ESLBM_ERR_ARG;
+    Counters c;
+    BCK(cudaMemcpyAsync(&c, b->counters(), sizeof(c), cudaMemcpyDeviceToHost, b->stream), "counters");
+    BCK(cudaStreamSynchronize(b->stream), "sync");
+    std::memset(out, 0, sizeof(*out));
+    out->fallbacks = c.fallbacks;
+    out->omega_min = out->omega_max = 0.0;
+    return c.fallbacks ? ESLBM_WARN_OMEGA_FALLBACK : ESLBM_OK;
+}
+
+}  // extern "C"

@@ -118,6 +118,27 @@ cudaError_t launch_adjoint_readout(int dim, bool fp64, const double *lam, void *
     return cudaGetLastError();
 }
 
+cudaError_t batch_scalar(int, bool, bool, const BatchLaunch &);
+cudaError_t batch_sw(int, bool, bool, const BatchLaunch &);
+int batch_occ_scalar(int, bool, bool);
+int batch_occ_sw(int, bool, bool);
+
+cudaError_t launch_batch_step(int family, bool fp64, bool entropic, const BatchLaunch &L)
+{
+    if (family == FAM_SW2) return batch_sw(family, fp64, entropic, L);
+    if (family == FAM_EULER2) return batch_family<Euler2>(fp64, false, L);
+    if (family == FAM_LINEAR2 || family == FAM_BURGERS2) return batch_scalar(family, fp64, entropic, L);
+    return cudaErrorInvalidValue;
+}
+
+int batch_blocks_per_sm(int family, bool fp64, bool entropic)
+{
+    if (family == FAM_SW2) return batch_occ_sw(family, fp64, entropic);
+    if (family == FAM_EULER2) return batch_occ_family<Euler2>(fp64, false);
+    if (family == FAM_LINEAR2 || family == FAM_BURGERS2) return batch_occ_scalar(family, fp64, entropic);
+    return 0;
+}
+
 int totals_blocks() { return kRedBlocks; }
 
 }  // namespace eslbm

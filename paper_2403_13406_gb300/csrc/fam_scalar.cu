@@ -44,6 +44,20 @@ cudaError_t adjoint_init_scalar(int family, bool fp64, const double *u0, const v
     return cudaErrorInvalidValue;
 }
 
+cudaError_t batch_scalar(int family, bool fp64, bool entropic, const BatchLaunch &L)
+{
+    if (family == FAM_LINEAR2) return batch_family<Scalar<2, false>>(fp64, entropic, L);
+    if (family == FAM_BURGERS2) return batch_family<Scalar<2, true>>(fp64, entropic, L);
+    return cudaErrorInvalidValue;
+}
+
+int batch_occ_scalar(int family, bool fp64, bool entropic)
+{
+    if (family == FAM_LINEAR2) return batch_occ_family<Scalar<2, false>>(fp64, entropic);
+    if (family == FAM_BURGERS2) return batch_occ_family<Scalar<2, true>>(fp64, entropic);
+    return 0;
+}
+
 cudaError_t init_scalar(int family, bool fp64, const double *u0, void *f, int64_t ncell, const Params &P,
                         Counters *cnt, cudaStream_t st)
 {

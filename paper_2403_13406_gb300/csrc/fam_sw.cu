@@ -31,6 +31,18 @@ cudaError_t adjoint_init_sw(int family, bool fp64, const double *u0, const void 
     return cudaErrorInvalidValue;
 }
 
+cudaError_t batch_sw(int family, bool fp64, bool entropic, const BatchLaunch &L)
+{
+    if (family == FAM_SW2) return batch_family<ShallowWater<2>>(fp64, entropic, L);
+    return cudaErrorInvalidValue;
+}
+
+int batch_occ_sw(int family, bool fp64, bool entropic)
+{
+    if (family == FAM_SW2) return batch_occ_family<ShallowWater<2>>(fp64, entropic);
+    return 0;
+}
+
 cudaError_t init_sw(int family, bool fp64, const double *u0, void *f, int64_t ncell, const Params &P,
                     Counters *cnt, cudaStream_t st)
 {

@@ -119,6 +119,50 @@ cudaError_t adjoint_init_family(bool fp64, const double *u0, const void *g, doub
     return cudaGetLastError();
 }
 
+template <class Sys, class R, bool ENT>
+cudaError_t batch_one(const BatchLaunch &L)
+{
+    BatchArgs<R> a{{(R *)L.pool[0], (R *)L.pool[1]}, L.inst, L.items, L.n_items, L.side, L.cnt};
+    StageList sl = L.sl;
+    ParamsR<R> P = params_as<R>(L.P);
+    void *args[] = {&a, &sl, &P};
+    return cudaLaunchCooperativeKernel((const void *)k_batch_step<Sys, R, ENT>, dim3((unsigned)L.grid), dim3(kBlock),
+                                       args, 0, L.stream);
+}
+
+template <class Sys, class R, bool ENT>
+int batch_occupancy()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<Sys, R, ENT>, kBlock, 0) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+template <class Sys>
+cudaError_t batch_family(bool fp64, bool entropic, const BatchLaunch &L)
+{
+    if constexpr (Sys::LINEAR || Sys::M == 4) {
+        (void)entropic;
+        return fp64 ? batch_one<Sys, double, false>(L) : batch_one<Sys, float, false>(L);
+    } else {
+        if (fp64) return entropic ? batch_one<Sys, double, true>(L) : batch_one<Sys, double, false>(L);
+        return entropic ? batch_one<Sys, float, true>(L) : batch_one<Sys, float, false>(L);
+    }
+}
+
+template <class Sys>
+int batch_occ_family(bool fp64, bool entropic)
+{
+    if constexpr (Sys::LINEAR || Sys::M == 4) {
+        (void)entropic;
+        return fp64 ? batch_occupancy<Sys, double, false>() : batch_occupancy<Sys, float, false>();
+    } else {
+        if (fp64) return entropic ? batch_occupancy<Sys, double, true>() : batch_occupancy<Sys, double, false>();
+        return entropic ? batch_occupancy<Sys, float, true>() : batch_occupancy<Sys, float, false>();
+    }
+}
+
 template <class Sys>
 cudaError_t init_family(bool fp64, const double *u0, void *f, int64_t ncell, const Params &P, Counters *cnt,
                         cudaStream_t st)

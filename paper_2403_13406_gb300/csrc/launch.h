@@ -70,6 +70,24 @@ cudaError_t launch_adjoint_readout(int dim, bool fp64, const double *lam, void *
 cudaError_t launch_adjoint_init(int family, bool fp64, const double *u0, const void *g, double *du0, int64_t ncell,
                                 const Params &P, cudaStream_t st);
 
+struct BatchLaunch {
+    void *pool[2];
+    const BatchInstance *inst;  // device array
+    const BatchItem *items;     // device array
+    int n_items;
+    int side;
+    Counters *cnt;
+    StageList sl;
+    Params P;
+    int grid;  // blocks (all resident: cooperative launch)
+    cudaStream_t stream;
+};
+
+// one composite step of every instance of a 2D batch (cooperative, grid.sync between stages)
+cudaError_t launch_batch_step(int family, bool fp64, bool entropic, const BatchLaunch &L);
+// resident blocks per SM of that kernel (0 if the family has no batched kernel)
+int batch_blocks_per_sm(int family, bool fp64, bool entropic);
+
 int totals_blocks();
 
 }  // namespace eslbm

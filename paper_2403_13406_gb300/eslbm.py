@@ -26,7 +26,11 @@ EXPORTS = ("eslbm_abi_version", "eslbm_status_string", "eslbm_query", "eslbm_cre
            "eslbm_set_stream", "eslbm_last_error", "eslbm_init_equilibrium", "eslbm_init_distributions",
            "eslbm_step", "eslbm_transport", "eslbm_relax", "eslbm_read_moments", "eslbm_read_distributions",
            "eslbm_read_totals", "eslbm_get_diagnostics", "eslbm_reset_diagnostics", "eslbm_use_graph",
-           "eslbm_read_totals_noalloc", "eslbm_gradient_workspace", "eslbm_gradient")
+           "eslbm_read_totals_noalloc", "eslbm_gradient_workspace", "eslbm_gradient",
+           "eslbm_batch_query", "eslbm_batch_create", "eslbm_batch_destroy", "eslbm_batch_last_error",
+           "eslbm_batch_init_equilibrium", "eslbm_batch_step", "eslbm_batch_read_moments",
+           "eslbm_batch_set_schedule", "eslbm_batch_get_schedule", "eslbm_batch_tune", "eslbm_batch_use_graph",
+           "eslbm_batch_gradient_workspace", "eslbm_batch_gradient", "eslbm_batch_get_diagnostics")
 
 
 class Config(ctypes.Structure):
@@ -49,6 +53,13 @@ class Diagnostics(ctypes.Structure):
     _fields_ = [("relaxations", ctypes.c_uint64), ("fallbacks", ctypes.c_uint64),
                 ("entropy_increases", ctypes.c_uint64), ("omega_min", ctypes.c_double),
                 ("omega_max", ctypes.c_double)]
+
+
+class BatchSizes(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("q", ctypes.c_int64), ("M", ctypes.c_int64),
+                ("planes", ctypes.c_int64), ("total_cells", ctypes.c_int64), ("pool_bytes", ctypes.c_uint64),
+                ("workspace_bytes", ctypes.c_uint64), ("stages_per_step", ctypes.c_int64),
+                ("step_cells", ctypes.c_int64)]
 
 
 _lib = None
@@ -87,6 +98,23 @@ def lib():
         "eslbm_gradient_workspace": (ctypes.c_int, [ctypes.POINTER(Config), i64, i64,
                                                     ctypes.POINTER(ctypes.c_uint64)]),
         "eslbm_gradient": (ctypes.c_int, [H, vp, vp, vp, i64, i64, vp, ctypes.c_uint64]),
+        "eslbm_batch_query": (ctypes.c_int, [ctypes.POINTER(Config), i32, vp, vp, ctypes.POINTER(BatchSizes)]),
+        "eslbm_batch_create": (ctypes.c_int, [ctypes.POINTER(Config), i32, vp, vp, vp, vp, vp, vp,
+                                              ctypes.POINTER(H)]),
+        "eslbm_batch_destroy": (ctypes.c_int, [H]),
+        "eslbm_batch_last_error": (ctypes.c_char_p, [H]),
+        "eslbm_batch_init_equilibrium": (ctypes.c_int, [H, vp, i32]),
+        "eslbm_batch_step": (ctypes.c_int, [H, i64]),
+        "eslbm_batch_read_moments": (ctypes.c_int, [H, vp, i32]),
+        "eslbm_batch_set_schedule": (ctypes.c_int, [H, i64, i32, i32]),
+        "eslbm_batch_get_schedule": (ctypes.c_int, [H, ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                                    ctypes.POINTER(i32)]),
+        "eslbm_batch_tune": (ctypes.c_int, [H, vp, ctypes.c_uint64, i32]),
+        "eslbm_batch_use_graph": (ctypes.c_int, [H, i32]),
+        "eslbm_batch_gradient_workspace": (ctypes.c_int, [ctypes.POINTER(Config), i32, vp, vp, i64, i64,
+                                                          ctypes.POINTER(ctypes.c_uint64)]),
+        "eslbm_batch_gradient": (ctypes.c_int, [H, vp, vp, vp, i64, i64, vp, ctypes.c_uint64]),
+        "eslbm_batch_get_diagnostics": (ctypes.c_int, [H, ctypes.POINTER(Diagnostics)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -283,4 +311,135 @@ class Simulation:
         out = torch.empty(shape, dtype=torch.float64, device=self.device)
         self._check(lib().eslbm_gradient(self.h, u0.data_ptr(), g.data_ptr(), out.data_ptr(), int(n), int(K), ptr,
                                          nb.value))
+        return out
+
+
+def _aligned(torch, nbytes, device, align=256):
+    """(tensor, pointer aligned to `align`) of a device byte buffer of at least nbytes."""
+    t = torch.empty(int(nbytes) + align, dtype=torch.uint8, device=device)
+    return t, (t.data_ptr() + align - 1) // align * align
+
+
+class Batch:
+    """Many independent 2D lattices of one configuration (sizes (nx[i], ny[i])) advanced by one
+    cooperative launch per composite step; pools and workspace are torch CUDA tensors."""
+
+    def __init__(self, cfg, sizes, stream=None, device=None):
+        import torch
+        self.torch = torch
+        self.cfg = cfg
+        self.shapes = [(int(ny), int(nx)) for nx, ny in sizes]
+        self.count = len(self.shapes)
+        self._nx = (ctypes.c_int64 * self.count)(*[s[1] for s in self.shapes])
+        self._ny = (ctypes.c_int64 * self.count)(*[s[0] for s in self.shapes])
+        bs = BatchSizes()
+        st = lib().eslbm_batch_query(ctypes.byref(cfg), self.count, self._nx, self._ny, ctypes.byref(bs))
+        if st != OK:
+            raise EslbmError(st, lib().eslbm_status_string(st).decode())
+        self.sizes = bs
+        self.device = torch.device(device or "cuda")
+        self._pa, pa = _aligned(torch, bs.pool_bytes, self.device)
+        self._pb, pb = _aligned(torch, bs.pool_bytes, self.device)
+        self._ws, ws = _aligned(torch, bs.workspace_bytes, self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        st = lib().eslbm_batch_create(ctypes.byref(cfg), self.count, self._nx, self._ny, pa, pb, ws,
+                                      self.stream.cuda_stream, ctypes.byref(h))
+        if st != OK:
+            raise EslbmError(st, lib().eslbm_status_string(st).decode())
+        self.h = h
+
+    @property
+    def M(self):
+        return int(self.sizes.M)
+
+    @property
+    def total_cells(self):
+        return int(self.sizes.total_cells)
+
+    def _check(self, st):
+        if st in (OK, WARN_OMEGA_FALLBACK):
+            return st
+        msg = lib().eslbm_status_string(st).decode()
+        if getattr(self, "h", None) is not None:
+            msg += ": " + lib().eslbm_batch_last_error(self.h).decode()
+        raise EslbmError(st, msg)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            lib().eslbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pack(self, fields):
+        """One flat float64 CUDA tensor from per-instance (M, ny, nx) fields."""
+        torch = self.torch
+        return torch.cat([torch.as_tensor(f, dtype=torch.float64).to(self.device).reshape(-1) for f in fields])
+
+    def unpack(self, flat):
+        """Per-instance (M, ny, nx) views of a flat tensor."""
+        out, o = [], 0
+        for ny, nx in self.shapes:
+            n = self.M * ny * nx
+            out.append(flat[o:o + n].reshape(self.M, ny, nx))
+            o += n
+        return out
+
+    def init_equilibrium(self, fields):
+        flat = fields if isinstance(fields, self.torch.Tensor) and fields.dim() == 1 else self.pack(fields)
+        flat = flat.to(device=self.device, dtype=self.torch.float64).contiguous()
+        return self._check(lib().eslbm_batch_init_equilibrium(self.h, flat.data_ptr(), 1))
+
+    def step(self, n=1):
+        return self._check(lib().eslbm_batch_step(self.h, int(n)))
+
+    def moments_flat(self, out=None):
+        t = out if out is not None else self.torch.empty(self.M * self.total_cells, dtype=self.torch.float64,
+                                                         device=self.device)
+        self._check(lib().eslbm_batch_read_moments(self.h, t.data_ptr(), 1))
+        return t
+
+    def moments(self):
+        return self.unpack(self.moments_flat())
+
+    def set_schedule(self, segment, blocks_per_sm, order):
+        return self._check(lib().eslbm_batch_set_schedule(self.h, int(segment), int(blocks_per_sm), int(order)))
+
+    def schedule(self):
+        seg, bps, order = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(lib().eslbm_batch_get_schedule(self.h, ctypes.byref(seg), ctypes.byref(bps), ctypes.byref(order)))
+        return int(seg.value), int(bps.value), int(order.value)
+
+    def tune(self, steps=2):
+        keep, p = _aligned(self.torch, self.sizes.pool_bytes, self.device)
+        self._check(lib().eslbm_batch_tune(self.h, p, int(self.sizes.pool_bytes), int(steps)))
+        return self.schedule()
+
+    def use_graph(self, enable=True):
+        return self._check(lib().eslbm_batch_use_graph(self.h, 1 if enable else 0))
+
+    def diagnostics(self):
+        d = Diagnostics()
+        st = lib().eslbm_batch_get_diagnostics(self.h, ctypes.byref(d))
+        self._check(st)
+        return {"fallbacks": d.fallbacks, "status": st}
+
+    def gradient(self, u0, dJ_duT, n, K=50):
+        """Per-instance dJ/du0 (flat float64 CUDA tensor; inputs flat or per-instance lists)."""
+        torch = self.torch
+        nb = ctypes.c_uint64()
+        self._check(lib().eslbm_batch_gradient_workspace(ctypes.byref(self.cfg), self.count, self._nx, self._ny,
+                                                         int(n), int(K), ctypes.byref(nb)))
+        keep, ws = _aligned(torch, nb.value, self.device)
+        flat = lambda x: (x if isinstance(x, torch.Tensor) and x.dim() == 1 else self.pack(x)).to(
+            device=self.device, dtype=torch.float64).contiguous()
+        u0, g = flat(u0), flat(dJ_duT)
+        out = torch.empty_like(u0)
+        self._check(lib().eslbm_batch_gradient(self.h, u0.data_ptr(), g.data_ptr(), out.data_ptr(), int(n), int(K),
+                                               ws, nb.value))
         return out

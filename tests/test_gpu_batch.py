@@ -1,0 +1,177 @@
+"""Batched execution: many uneven 2D lattices advanced by one cooperative launch per step.
+
+Every instance must compute what a single handle of its size computes (the same
+stage list and per-cell arithmetic): bitwise for fixed omega, and within the
+parity bars for the entropic omega, whose root search may be contracted
+differently by the compiler in the two kernels.  The schedule (segment length,
+residency, order of the work list) does not change any result bitwise, the
+autotuner restores the state it times from, and an instance of the batch matches
+the FP64 oracle directly.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2403_13406_gb300 import eslbm, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+SIZES = [(33, 27), (64, 64), (130, 7), (17, 90), (257, 3), (1, 5)]
+SYSTEMS = {
+    # amplitudes keep every cell's entropic root well inside [0, t_max] and the convexity domain:
+    # where a root's existence is decided within rounding (the fallback), two differently
+    # contracted kernels may decide differently, and the comparison would test rounding only
+    "sw": (dict(V=8.0, g=9.81), lambda nx, ny, i: inputs.sw_random_2d(nx, ny, seed=100 + i, h_amp=0.03,
+                                                                      u_amp=0.03)),
+    "burgers": (dict(V=3.0, c=(1.0, 0.6)), lambda nx, ny, i: inputs.burgers_2d(nx, ny, seed=200 + i)),
+    "linear": (dict(V=1.0, a=(0.2, -0.15)), lambda nx, ny, i: inputs.linear_sine_2d(nx, ny) * (1 + 0.1 * i)),
+}
+TOL = {"fp64": 1e-13, "fp32": 2e-5}
+
+
+def rel_max(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def fields(system, sizes):
+    return [SYSTEMS[system][1](nx, ny, i) for i, (nx, ny) in enumerate(sizes)]
+
+
+def make_batch(system, mode, precision, sizes=SIZES, scheme="I"):
+    cfg = eslbm.make_config(2, system, 1, 1, precision=precision, omega_mode=mode, scheme=scheme,
+                            **SYSTEMS[system][0])
+    return eslbm.Batch(cfg, sizes)
+
+
+def single(system, mode, precision, nx, ny, u0, n, scheme="I"):
+    cfg = eslbm.make_config(2, system, nx, ny, precision=precision, omega_mode=mode, scheme=scheme,
+                            **SYSTEMS[system][0])
+    sim = eslbm.Simulation(cfg)
+    sim.init_equilibrium(u0)
+    sim.step(n)
+    u = sim.moments(host=True)
+    sim.close()
+    return u
+
+
+@pytest.mark.parametrize("system", list(SYSTEMS))
+@pytest.mark.parametrize("mode", ["fixed", "entropic"])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_matches_single_handles(system, mode, precision):
+    u0 = fields(system, SIZES)
+    b = make_batch(system, mode, precision)
+    b.init_equilibrium(u0)
+    b.step(3)
+    got = [u.cpu().numpy() for u in b.moments()]
+    if system == "sw":
+        assert b.diagnostics()["fallbacks"] == 0  # the data keeps every root inside the bracket
+    b.close()
+    for (nx, ny), u, g in zip(SIZES, u0, got):
+        ref = single(system, mode, precision, nx, ny, u, 3)
+        assert g.shape == ref.shape
+        if mode == "fixed" or system == "linear":
+            assert np.array_equal(g, ref), (nx, ny)
+        else:
+            assert rel_max(g, ref) <= TOL[precision], (nx, ny)
+
+
+@pytest.mark.parametrize("scheme", ["II", "IV", "plain", "B"])
+def test_batch_scheme_variants(scheme):
+    u0 = fields("sw", SIZES[:3])
+    b = make_batch("sw", "fixed", "fp64", SIZES[:3], scheme=scheme)
+    b.init_equilibrium(u0)
+    b.step(2)
+    got = [u.cpu().numpy() for u in b.moments()]
+    b.close()
+    for (nx, ny), u, g in zip(SIZES[:3], u0, got):
+        assert np.array_equal(g, single("sw", "fixed", "fp64", nx, ny, u, 2, scheme=scheme))
+
+
+def test_batch_instance_matches_oracle_fp64():
+    """One instance of an entropic FP64 batch against the oracle (1e-12 relative max-norm)."""
+    sizes = [(40, 31), (29, 50)]
+    u0 = fields("sw", sizes)
+    b = make_batch("sw", "entropic", "fp64", sizes)
+    b.init_equilibrium(u0)
+    b.step(2)
+    got = [u.cpu().numpy() for u in b.moments()]
+    b.close()
+    for (nx, ny), u, g in zip(sizes, u0, got):
+        m = O.Model(2, "sw", nx, ny, omega_mode="entropic", **SYSTEMS["sw"][0])
+        f = O.init_equilibrium(m, u)
+        O.composite_steps(m, f, 2)
+        assert rel_max(g, O.moments(m, f)) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_schedule_invariance_bitwise(precision):
+    u0 = fields("sw", SIZES)
+    results = []
+    b = make_batch("sw", "entropic", precision)
+    full = b.schedule()[1]  # the default schedule runs at the kernel's full residency
+    for seg, bps, order in [(256, full, 0), (128, 1, 1), (1024, full, 1), (512, max(1, full // 2), 0)]:
+        b.set_schedule(seg, bps, order)
+        b.init_equilibrium(u0)
+        b.step(2)
+        results.append(b.moments_flat().cpu().numpy())
+    b.close()
+    for r in results[1:]:
+        assert np.array_equal(r, results[0])
+
+
+def test_graph_replay_and_tune_keep_results():
+    u0 = fields("burgers", SIZES)
+    b = make_batch("burgers", "entropic", "fp32")
+    b.init_equilibrium(u0)
+    b.step(1)
+    before = b.moments_flat().cpu().numpy()
+    sched = b.tune(steps=1)
+    assert sched[0] in (128, 256, 512, 1024) and sched[2] in (0, 1)
+    assert np.array_equal(b.moments_flat().cpu().numpy(), before)  # the tuner restores the state
+    b.step(2)
+    direct = b.moments_flat().cpu().numpy()
+    b.init_equilibrium(u0)
+    b.use_graph(True)
+    b.step(1)
+    b.step(2)
+    graphed = b.moments_flat().cpu().numpy()
+    b.close()
+    assert np.array_equal(graphed, direct)
+
+
+def test_batch_gradient_matches_single_handles():
+    sizes = [(24, 17), (13, 30)]
+    u0 = fields("sw", sizes)
+    rng = np.random.default_rng(7)
+    cot = [rng.standard_normal(u.shape) for u in u0]
+    b = make_batch("sw", "entropic", "fp64", sizes)
+    g = b.unpack(b.gradient(u0, cot, n=5, K=2))
+    after = b.moments_flat().cpu().numpy()
+    b.init_equilibrium(u0)
+    assert np.array_equal(after, b.moments_flat().cpu().numpy())  # back at f^eq(u0)
+    for (nx, ny), u, c, gi in zip(sizes, u0, cot, g):
+        cfg = eslbm.make_config(2, "sw", nx, ny, precision="fp64", omega_mode="entropic", **SYSTEMS["sw"][0])
+        sim = eslbm.Simulation(cfg)
+        ref = sim.gradient(torch.as_tensor(u, device="cuda"), torch.as_tensor(c, device="cuda"), n=5, K=2)
+        sim.close()
+        assert torch.equal(gi, ref)
+
+
+def test_batch_errors():
+    cfg1 = eslbm.make_config(1, "sw", 64, 1, V=8.0, g=9.81)
+    with pytest.raises(eslbm.EslbmError) as e:
+        eslbm.Batch(cfg1, [(64, 1)])
+    assert e.value.status == eslbm.ERR_UNSUPPORTED
+    b = make_batch("sw", "entropic", "fp32", SIZES[:2])
+    bad = fields("sw", SIZES[:2])
+    bad[1][0, 3, 4] = -1.0  # negative depth: outside the domain
+    with pytest.raises(eslbm.EslbmError) as e:
+        b.init_equilibrium(bad)
+    assert e.value.status == eslbm.ERR_DOMAIN
+    with pytest.raises(eslbm.EslbmError):
+        b.set_schedule(64, 1, 0)  # segment below 128
+    b.close()
