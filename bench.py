@@ -35,6 +35,7 @@ METRIC = "composite-step site updates/s + HBM GB/s fraction; FP32 vs FP64 at sta
 UNIT = "site_updates/s"
 N_CELLS = 1 << 20
 V, G, T_FINAL = 4.0, 9.81, 0.05
+U_REF = (1.0, 0.0)  # reference state of the shifted FP32 storage: the background depth at rest
 BATCH_V = 8.0  # lattice velocity of the batched 2D shallow-water instances: sqrt(9.81 x 1.05) < V/2
 L2_FLUSH_BYTES = 512 << 20
 # FP32 roofline of the dominant kernel (the fused composite step k_step1d, entropic shallow water):
@@ -54,9 +55,10 @@ def parse():
     p.add_argument("--n", type=int, default=N_CELLS)
     p.add_argument("--t-final", type=float, default=T_FINAL)
     p.add_argument("--no-extras", action="store_true", help="skip the FP64 and CPU baseline legs")
-    p.add_argument("--leg", default=None, choices=["hbm2d", "batched"],
+    p.add_argument("--leg", default=None, choices=["hbm2d", "batched", "fp32err"],
                    help="run one secondary measurement alone and print its JSON (for profiling)")
     p.add_argument("--hbm-steps", type=int, default=20, help="composite steps of the 2D streaming leg")
+    p.add_argument("--hbm-case", default=None, help="one case of the 2D streaming leg (default: all)")
     return p.parse_args()
 
 
@@ -187,8 +189,9 @@ def main():
         torch.cuda.set_device(0)
         dev = torch.device("cuda", 0)
         stream = torch.cuda.Stream(device=dev)
-        leg = hbm2d_leg if args.leg == "hbm2d" else batch_leg
-        kw = {"steps": args.hbm_steps} if args.leg == "hbm2d" else {}
+        leg = {"hbm2d": hbm2d_leg, "batched": batch_leg, "fp32err": fp32err_leg}[args.leg]
+        kw = ({"steps": args.hbm_steps, "only": args.hbm_case} if args.leg == "hbm2d" else
+              {"N": args.n, "t_final": args.t_final} if args.leg == "fp32err" else {})
         print(json.dumps(leg(torch, eslbm, inputs, stream, dev, **kw)), flush=True)
         return
 
@@ -207,7 +210,7 @@ def main():
 
     N = args.n
     n_steps = inputs.steps_for(args.t_final, 1.0 / N, V)
-    cfg = eslbm.make_config(1, "sw", N, V=V, g=G, precision="fp32", omega_mode="entropic")
+    cfg = eslbm.make_config(1, "sw", N, V=V, g=G, precision="fp32", omega_mode="entropic", u_ref=U_REF)
     with torch.cuda.stream(stream):
         sim = eslbm.Simulation(cfg, stream=stream, device=dev)
         sim.use_graph(True)
@@ -297,6 +300,7 @@ def main():
     extras = {}
     if not args.no_extras and rank == 0:
         extras = fp64_leg(sim, torch, eslbm, inputs, stream, dev, N)
+        extras.update(accuracy_leg(torch, eslbm, inputs, stream, dev))
         extras.update(adjoint_leg(torch, eslbm, inputs, stream, dev))
         extras.update(batch_leg(torch, eslbm, inputs, stream, dev))
         extras.update(hbm2d_leg(torch, eslbm, inputs, stream, dev))
@@ -313,6 +317,7 @@ def main():
                 "config": {"workload": "sw1d_d1q2_entropic_n%d_t%g" % (N, args.t_final), "system": "shallow_water",
                            "lattice": "D1Q2", "N": N, "V": V, "g": G, "t_final": args.t_final,
                            "composite_steps": n_steps, "stages": stages, "omega": "entropic", "precision": "fp32",
+                           "storage": "shifted, u_ref = (1, 0)",
                            "cuda_graph": True, "parallelism": "replicas" if world > 1 else "single",
                            "l2": "flushed between timed steps; the 16 MB state stays L2-resident inside a step"},
                 "roofline": roofline, "cpu_baseline": cpu,
@@ -334,7 +339,7 @@ def fp64_leg(sim32, torch, eslbm, inputs, stream, dev, N, nsteps=60):
     for name, prec, scheme, steps in (("fp64_composite", "fp64", "I", nsteps), ("fp32_composite", "fp32", "I", nsteps),
                                       ("fp64_plain", "fp64", "plain", 24 * nsteps)):
         cfg = eslbm.make_config(1, "sw", N, V=V, g=G, precision=prec, omega_mode="entropic" if scheme == "I" else "fixed",
-                                scheme=scheme)
+                                scheme=scheme, u_ref=U_REF if prec == "fp32" else None)
         with torch.cuda.stream(stream):
             sim = eslbm.Simulation(cfg, stream=stream, device=dev)
             sim.use_graph(True)
@@ -358,6 +363,96 @@ def fp64_leg(sim32, torch, eslbm, inputs, stream, dev, N, nsteps=60):
     out["fp32_composite"]["rel_l2_h_vs_fp64"] = float(np.linalg.norm(res["fp32_composite"][0] - ref) / nrm)
     out["fp64_plain"]["rel_l2_h_vs_fp64_composite"] = float(np.linalg.norm(res["fp64_plain"][0] - ref) / nrm)
     return {"fp32_vs_fp64": {"N": N, "t": nsteps * 24.0 / N / V, **out}}
+
+
+def fp32err_leg(torch, eslbm, inputs, stream, dev, N=N_CELLS, t_final=T_FINAL):
+    """Error of the FP32 composite solution against the FP64 composite solution of the bench workload
+    (1D shallow water, entropic omega) at the final time, relative L2 of h and of hu, with the error after
+    1/8, 1/4, 1/2 of the steps (rounding accumulates with the number of stages).  FP64 runs at 1/64 of
+    the FP32 rate on this GPU, so the full-size case takes minutes."""
+    n_steps = inputs.steps_for(t_final, 1.0 / N, V)
+    marks = sorted(set([max(1, n_steps // 8), max(1, n_steps // 4), max(1, n_steps // 2), n_steps]))
+    u0 = torch.from_numpy(inputs.sw_sine_1d(N, 1.0, 0.1)).to(dev)
+    res = {}
+    for prec in ("fp32", "fp32_shifted", "fp64"):
+        cfg = eslbm.make_config(1, "sw", N, V=V, g=G, precision=prec[:4], omega_mode="entropic",
+                                u_ref=U_REF if prec == "fp32_shifted" else None)
+        with torch.cuda.stream(stream):
+            sim = eslbm.Simulation(cfg, stream=stream, device=dev)
+            sim.use_graph(True)
+            sim.init_equilibrium(u0)
+            done, out = 0, []
+            for mk in marks:
+                sim.step(mk - done)
+                done = mk
+                out.append(sim.moments().cpu().numpy())
+            res[prec] = out
+            sim.close()
+    rows = []
+    for i, mk in enumerate(marks):
+        b = res["fp64"][i]
+        row = {"steps": mk, "t": mk * 24.0 / N / V}
+        for name in ("fp32", "fp32_shifted"):
+            a = res[name][i]
+            row[name] = {"rel_l2_h": float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0])),
+                         "rel_l2_hu": float(np.linalg.norm(a[1] - b[1]) / max(np.linalg.norm(b[1]), 1e-300)),
+                         "rel_l2_state": float(np.linalg.norm(a - b) / np.linalg.norm(b))}
+        rows.append(row)
+    return {"fp32_error": {"N": N, "t_final": t_final, "reference": "fp64 composite (same scheme, same grid)",
+                           "rows": rows}}
+
+
+def accuracy_leg(torch, eslbm, inputs, stream, dev, n_ref=1 << 16, sizes=tuple(1 << k for k in range(8, 17)),
+                 targets=(1e-5, 1e-6, 1e-7)):
+    """Time to solution at a stated L2 error: the FP32 composite scheme (entropic omega) against the FP64
+    plain second-order scheme R T (omega = 2, 24 plain steps per composite step, so both reach the same
+    time t = 2 x 24 / (256 V) = 0.046875 on every grid), 1D shallow water h0 = 1 + 0.1 sin 2 pi x.  The
+    error is the relative discrete L2 norm of h against the FP64 composite solution on 2^16 cells, sampled
+    at the coarse points (cells at j dx on every grid).  Times are CUDA-event times of the steps alone."""
+    def run(N, prec, scheme, n_comp):
+        cfg = eslbm.make_config(1, "sw", N, V=V, g=G, precision=prec,
+                                omega_mode="entropic" if scheme == "I" else "fixed", omega=2.0, scheme=scheme,
+                                u_ref=U_REF if prec == "fp32" else None)
+        steps = n_comp if scheme == "I" else 24 * n_comp
+        with torch.cuda.stream(stream):
+            sim = eslbm.Simulation(cfg, stream=stream, device=dev)
+            sim.use_graph(True)
+            u0 = torch.from_numpy(inputs.sw_sine_1d(N, 1.0, 0.1)).to(dev)
+            sim.init_equilibrium(u0)
+            sim.step(1)  # warm-up and graph capture
+            sim.init_equilibrium(u0)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            h = sim.moments().cpu().numpy()[0]
+            sim.close()
+        return h, e0.elapsed_time(e1)
+
+    n_at = lambda N: 2 * N // 256  # composite steps to t = 0.046875
+    ref, _ = run(n_ref, "fp64", "I", n_at(n_ref))
+    rows = []
+    for N in sizes:
+        r = ref[:: n_ref // N]
+        row = {"N": N}
+        for name, prec, scheme in (("fp32_composite", "fp32", "I"), ("fp64_plain", "fp64", "plain")):
+            h, ms = run(N, prec, scheme, n_at(N))
+            row[name] = {"rel_l2": float(np.linalg.norm(h - r) / np.linalg.norm(r)), "ms": ms}
+        rows.append(row)
+    best = {}
+    for eps in targets:
+        pick = {}
+        for name in ("fp32_composite", "fp64_plain"):
+            ok = [r for r in rows if r[name]["rel_l2"] <= eps]
+            pick[name] = ({"N": ok[0]["N"], "ms": ok[0][name]["ms"], "rel_l2": ok[0][name]["rel_l2"]} if ok
+                          else None)
+        if pick["fp32_composite"] and pick["fp64_plain"]:
+            pick["speedup_fp32_composite"] = pick["fp64_plain"]["ms"] / pick["fp32_composite"]["ms"]
+        best["%g" % eps] = pick
+    return {"time_to_accuracy": {"t": 2 * 24 / (256 * V), "reference": "fp64 composite, N = %d" % n_ref,
+                                 "sweep": rows, "at_target_rel_l2": best}}
 
 
 def adjoint_leg(torch, eslbm, inputs, stream, dev, N=1 << 16, n=96, K=16):
@@ -446,7 +541,7 @@ def batch_leg(torch, eslbm, inputs, stream, dev, count=64, steps=20, grad_instan
                                     "grad_norm": gnorm}}}
 
 
-def hbm2d_leg(torch, eslbm, inputs, stream, dev, steps=20):
+def hbm2d_leg(torch, eslbm, inputs, stream, dev, steps=20, only=None):
     """Per-stage streaming rate of the 2D stage kernel (one fused pull-shift + relax launch per stage,
     every distribution read and written once): D2Q4 Burgers 4096^2 FP32 (32 B per cell-stage) with
     omega = 2 and with the entropic omega, and D2Q4 Euler 8192^2 FP32 (128 B per cell-stage) with
@@ -461,6 +556,8 @@ def hbm2d_leg(torch, eslbm, inputs, stream, dev, steps=20):
               lambda n: inputs.euler_vortex_2d(n, n))]
     out = {}
     for name, dim, system, n, kw, mode, scheme, nsteps, init in cases:
+        if only and name != only:
+            continue
         cfg = eslbm.make_config(dim, system, n, n, precision="fp32", omega_mode=mode, scheme=scheme, **kw)
         with torch.cuda.stream(stream):
             sim = eslbm.Simulation(cfg, stream=stream, device=dev)

@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define ESLBM_ABI_VERSION 1
+#define ESLBM_ABI_VERSION 2
 
 typedef enum {
     ESLBM_OK = 0,
@@ -88,8 +88,22 @@ typedef struct {
     double gamma;       /* ratio of specific heats (Euler) */
     double t_max;       /* entropic mode: omega - 1 is searched in [0, t_max]; 0 -> 3 */
     int32_t diagnostics;/* 1: count per-cell entropy increases and track omega min/max */
-    int32_t reserved;
+    int32_t shifted;    /* 1: store g = f - fbar with fbar_k = f^eq_k(u_ref) (see below); 0: store f */
+    double u_ref[4];    /* reference conserved state of the shifted storage (M values used) */
 } eslbm_config;
+
+/* Shifted storage (no counterpart in the paper).  With shifted = 1 the state
+   buffers hold g_k = f_k - fbar_k, fbar_k = f^eq_k(u_ref) rounded to the storage
+   precision, and the relaxation works on deviations from the reference state
+   (the conserved moments as u_ref + sum_k g_k, the equilibrium as
+   f^eq(u) - f^eq(u_ref) in a cancellation-free form).  The rounding of the
+   stored values is then relative to |f - fbar| instead of |f|: for data close to
+   a background state (e.g. a depth of 1 plus waves of amplitude 0.1) the FP32
+   rounding error of a long run drops by the ratio of the two.  The scheme and
+   every call's inputs and outputs are unchanged (f and u in, f and u out); only
+   the raw buffers differ, so eslbm_read_totals_noalloc must receive the same
+   configuration.  u_ref must lie in the domain of Section 1.2 (else
+   ESLBM_ERR_DOMAIN from eslbm_query and eslbm_create). */
 
 typedef struct {
     int64_t q;               /* velocities: 2 (D1Q2) or 4 (D2Q4) */

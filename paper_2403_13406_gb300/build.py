@@ -16,7 +16,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libeslbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-Xcompiler", "-Wall", "-I", os.path.join(ROOT, "include")]
+         "-Xcompiler", "-Wall", "-Xcompiler", "-Wno-unknown-pragmas", "-I", os.path.join(ROOT, "include")]
 
 
 def nvcc():

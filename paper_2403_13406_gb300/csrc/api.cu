@@ -40,6 +40,7 @@ eslbm_status validate(const eslbm_config *c)
     if (!(c->V > 0.0) || !std::isfinite(c->V)) return ESLBM_ERR_ARG;
     if (c->omega_mode == ESLBM_OMEGA_FIXED && !(std::isfinite(c->omega))) return ESLBM_ERR_ARG;
     if (c->t_max < 0.0 || !std::isfinite(c->t_max)) return ESLBM_ERR_ARG;
+    if (c->shifted != 0 && c->shifted != 1) return ESLBM_ERR_ARG;
     if (c->system == ESLBM_SHALLOW_WATER && !(c->g > 0.0)) return ESLBM_ERR_ARG;
     if (c->system == ESLBM_EULER) {
         if (c->dim != 2) return ESLBM_ERR_UNSUPPORTED;
@@ -415,6 +416,8 @@ eslbm_status eslbm_query(const eslbm_config *cfg, eslbm_sizes *out)
     if (!out) return ESLBM_ERR_ARG;
     eslbm_status s = validate(cfg);
     if (s != ESLBM_OK) return s;
+    Params P;
+    if ((s = params_of(*cfg, P)) != ESLBM_OK) return s;  // checks the reference state
     eslbm_sizes z;
     z.q = cfg->dim == 1 ? 2 : 4;
     z.M = num_M(*cfg);
@@ -452,16 +455,10 @@ eslbm_status eslbm_create(const eslbm_config *cfg, void *f_a, void *f_b, void *w
     h->ws = (char *)workspace;
     h->stream = (cudaStream_t)stream;
     h->pending = 0;
-    h->P.V = cfg->V;
-    h->P.a[0] = cfg->a[0];
-    h->P.a[1] = cfg->a[1];
-    h->P.c[0] = cfg->c[0];
-    h->P.c[1] = cfg->c[1];
-    h->P.g = cfg->g;
-    h->P.gamma = cfg->gamma;
-    h->P.omega = cfg->omega;
-    h->P.t_max = cfg->t_max > 0.0 ? cfg->t_max : 3.0;
-    if (cfg->omega_mode == ESLBM_OMEGA_ENTROPIC && cfg->system == ESLBM_LINEAR) h->P.omega = 2.0;
+    if ((s = params_of(*cfg, h->P)) != ESLBM_OK) {
+        delete h;
+        return s;
+    }
     h->ops = scheme_ops(cfg->scheme, cfg->kappa);
     h->relaxations = 0;
     h->use_graph = false;
@@ -533,7 +530,9 @@ eslbm_status eslbm_init_distributions(eslbm_handle *h, const double *f0, int32_t
                "copy f0");
             src = (const double *)h->spare();
         }
-        CK(launch_set(h->fp64, src, (char *)h->f[h->cur] + (size_t)p * (size_t)n * elem, n, c, h->stream), "set");
+        CK(launch_set(h->fp64, src, (char *)h->f[h->cur] + (size_t)p * (size_t)n * elem, n, h->P.fbar[p], c,
+                      h->stream),
+           "set");
     }
     unsigned long long nf = 0;
     CK(cudaMemcpyAsync(&nf, &c->non_finite, sizeof(nf), cudaMemcpyDeviceToHost, h->stream), "read flag");
@@ -591,7 +590,7 @@ eslbm_status eslbm_read_moments(eslbm_handle *h, double *u_out, int32_t on_devic
     if (!h || !u_out) return fail(h, ESLBM_ERR_ARG, "null argument");
     double *dst = on_device ? u_out : (double *)h->spare();
     CK(launch_gather_moments(h->cfg.dim, h->fp64, h->f[h->cur], dst, h->cfg.nx, h->cfg.ny, (int)h->sz.M,
-                             make_shift(h, h->pending), h->stream),
+                             make_shift(h, h->pending), h->P.fbar, h->stream),
        "gather moments");
     if (!on_device) {
         CK(cudaMemcpyAsync(u_out, dst, sizeof(double) * (size_t)(h->sz.M * h->sz.ncell), cudaMemcpyDeviceToHost,
@@ -609,7 +608,7 @@ eslbm_status eslbm_read_distributions(eslbm_handle *h, double *f_out, int32_t on
     const int64_t n = h->sz.ncell;
     if (on_device) {
         CK(launch_gather_planes(h->cfg.dim, h->fp64, h->f[h->cur], f_out, h->cfg.nx, h->cfg.ny, (int)h->sz.M, 0,
-                                (int)h->sz.planes, sh, h->stream),
+                                (int)h->sz.planes, sh, h->P.fbar, h->stream),
            "gather planes");
         return ESLBM_OK;
     }
@@ -618,7 +617,7 @@ eslbm_status eslbm_read_distributions(eslbm_handle *h, double *f_out, int32_t on
     for (int64_t p = 0; p < h->sz.planes; p += per) {
         const int np = (int)std::min<int64_t>(per, h->sz.planes - p);
         CK(launch_gather_planes(h->cfg.dim, h->fp64, h->f[h->cur], (double *)h->spare(), h->cfg.nx, h->cfg.ny,
-                                (int)h->sz.M, (int)p, np, sh, h->stream),
+                                (int)h->sz.M, (int)p, np, sh, h->P.fbar, h->stream),
            "gather planes");
         CK(cudaMemcpyAsync(f_out + p * n, h->spare(), sizeof(double) * (size_t)(np * n), cudaMemcpyDeviceToHost,
                            h->stream),

@@ -276,15 +276,10 @@ eslbm_status eslbm_batch_create(const eslbm_config *base, int32_t count, const i
     b->ws = (char *)workspace;
     b->stream = (cudaStream_t)stream;
     b->pending = 0;
-    b->P.V = base->V;
-    b->P.a[0] = base->a[0];
-    b->P.a[1] = base->a[1];
-    b->P.c[0] = base->c[0];
-    b->P.c[1] = base->c[1];
-    b->P.g = base->g;
-    b->P.gamma = base->gamma;
-    b->P.omega = (b->entropic && base->system == ESLBM_LINEAR) ? 2.0 : base->omega;
-    b->P.t_max = base->t_max > 0.0 ? base->t_max : 3.0;
+    if ((s = params_of(*base, b->P)) != ESLBM_OK) {
+        delete b;
+        return s;
+    }
     b->ops = scheme_ops(base->scheme, base->kappa);
     b->use_graph = false;
     int dev = 0;
@@ -405,7 +400,7 @@ eslbm_status eslbm_batch_read_moments(eslbm_batch *b, double *u_out, int32_t on_
     for (int32_t i = 0; i < b->count; ++i) {
         const BatchInstance &I = b->L.inst[(size_t)i];
         BCK(launch_gather_moments(2, b->fp64, b->instance_ptr(b->side, i), dst + cell0 * b->L.M, I.nx, I.ny,
-                                  (int)b->L.M, shift_for(b, i, b->pending), b->stream),
+                                  (int)b->L.M, shift_for(b, i, b->pending), b->P.fbar, b->stream),
             "gather moments");
         cell0 += I.nx * I.ny;
     }

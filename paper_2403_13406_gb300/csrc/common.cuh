@@ -16,6 +16,17 @@ struct Params {
     double gamma;    // Euler
     double omega;    // fixed relaxation parameter
     double t_max;    // entropic search interval for omega - 1
+    // Shifted storage: the state holds g = f - fbar for a constant reference
+    // equilibrium fbar_k = f^eq_k(u_ref) (rounded to the storage precision), so
+    // that the storage rounding is relative to the deviation from the reference
+    // state instead of to f.  The relaxation then works on deviations:
+    // u = ubar + du with du = sum_k g_k + cm, and its target
+    // f^eq_k(u) - fbar_k = [f^eq_k(u) - f^eq_k(ubar)] + rdev_k with the bracket in
+    // deviation form (no cancellation).  ubar is sum_k fbar_k rounded to the
+    // storage precision, cm that rounding's residual, rdev_k = f^eq_k(ubar) - fbar_k.
+    int shifted;
+    double fbar[16], ubar[4], cm[4], rdev[16];
+    double aux[4];  // reference quantities of the deviation forms (velocities, pressure)
 };
 
 // The same parameters in the arithmetic type of a kernel (converted once on the
@@ -24,6 +35,8 @@ struct Params {
 template <class R> struct ParamsR {
     R V, inv2V, a[2], c[2], g, gamma_m1, omega, t_max;
     R gV4, inv16gV;  // 4 g V and 1 / (16 g V) (shallow water)
+    int shifted;     // see Params
+    R ubar[4], cm[4], rdev[16], fbar[16], aux[4];
 };
 
 template <class R> inline ParamsR<R> params_as(const Params &P)
@@ -41,6 +54,16 @@ template <class R> inline ParamsR<R> params_as(const Params &P)
     q.t_max = R(P.t_max);
     q.gV4 = R(4.0 * P.g * P.V);
     q.inv16gV = P.g > 0 ? R(1.0 / (16.0 * P.g * P.V)) : R(0);
+    q.shifted = P.shifted;
+    for (int i = 0; i < 4; ++i) {
+        q.ubar[i] = R(P.ubar[i]);
+        q.cm[i] = R(P.cm[i]);
+        q.aux[i] = R(P.aux[i]);
+    }
+    for (int i = 0; i < 16; ++i) {
+        q.rdev[i] = R(P.rdev[i]);
+        q.fbar[i] = R(P.fbar[i]);
+    }
     return q;
 }
 

@@ -1,5 +1,7 @@
 // fam_misc.cu -- Euler (fixed omega), gathers, conversion and the dispatch
 // entry points declared in launch.h.
+#include <cmath>
+
 #include "family_impl.cuh"
 
 namespace eslbm {
@@ -48,39 +50,119 @@ cudaError_t launch_totals(int family, bool fp64, const void *f, double *partials
 
 template <int DIM, class R, bool MOM>
 static cudaError_t gather_t(const void *f, double *out, int64_t nx, int64_t ny, int M, int p0, int np,
-                            const Shift &sh, cudaStream_t st)
+                            const Shift &sh, const double *fbar, cudaStream_t st)
 {
+    RefPlanes ref;
+    for (int i = 0; i < 16; ++i) ref.fbar[i] = fbar ? fbar[i] : 0.0;
     dim3 grid((unsigned)((nx + kBlock - 1) / kBlock), (unsigned)ny);
-    k_gather<DIM, R, MOM><<<grid, kBlock, 0, st>>>((const R *)f, out, nx, ny, M, p0, np, sh);
+    k_gather<DIM, R, MOM><<<grid, kBlock, 0, st>>>((const R *)f, out, nx, ny, M, p0, np, sh, ref);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather_moments(int dim, bool fp64, const void *f, double *out, int64_t nx, int64_t ny, int M,
-                                  const Shift &sh, cudaStream_t st)
+                                  const Shift &sh, const double *fbar, cudaStream_t st)
 {
     if (dim == 1)
-        return fp64 ? gather_t<1, double, true>(f, out, nx, ny, M, 0, 0, sh, st)
-                    : gather_t<1, float, true>(f, out, nx, ny, M, 0, 0, sh, st);
-    return fp64 ? gather_t<2, double, true>(f, out, nx, ny, M, 0, 0, sh, st)
-                : gather_t<2, float, true>(f, out, nx, ny, M, 0, 0, sh, st);
+        return fp64 ? gather_t<1, double, true>(f, out, nx, ny, M, 0, 0, sh, fbar, st)
+                    : gather_t<1, float, true>(f, out, nx, ny, M, 0, 0, sh, fbar, st);
+    return fp64 ? gather_t<2, double, true>(f, out, nx, ny, M, 0, 0, sh, fbar, st)
+                : gather_t<2, float, true>(f, out, nx, ny, M, 0, 0, sh, fbar, st);
 }
 
 cudaError_t launch_gather_planes(int dim, bool fp64, const void *f, double *out, int64_t nx, int64_t ny, int M,
-                                 int plane0, int nplanes, const Shift &sh, cudaStream_t st)
+                                 int plane0, int nplanes, const Shift &sh, const double *fbar, cudaStream_t st)
 {
     if (dim == 1)
-        return fp64 ? gather_t<1, double, false>(f, out, nx, ny, M, plane0, nplanes, sh, st)
-                    : gather_t<1, float, false>(f, out, nx, ny, M, plane0, nplanes, sh, st);
-    return fp64 ? gather_t<2, double, false>(f, out, nx, ny, M, plane0, nplanes, sh, st)
-                : gather_t<2, float, false>(f, out, nx, ny, M, plane0, nplanes, sh, st);
+        return fp64 ? gather_t<1, double, false>(f, out, nx, ny, M, plane0, nplanes, sh, fbar, st)
+                    : gather_t<1, float, false>(f, out, nx, ny, M, plane0, nplanes, sh, fbar, st);
+    return fp64 ? gather_t<2, double, false>(f, out, nx, ny, M, plane0, nplanes, sh, fbar, st)
+                : gather_t<2, float, false>(f, out, nx, ny, M, plane0, nplanes, sh, fbar, st);
 }
 
-cudaError_t launch_set(bool fp64, const double *src, void *f, int64_t n, Counters *cnt, cudaStream_t st)
+cudaError_t launch_set(bool fp64, const double *src, void *f, int64_t n, double offset, Counters *cnt,
+                       cudaStream_t st)
 {
     const unsigned grid = (unsigned)((n + kBlock - 1) / kBlock);
-    if (fp64) k_set<double><<<grid, kBlock, 0, st>>>(src, (double *)f, n, cnt);
-    else k_set<float><<<grid, kBlock, 0, st>>>(src, (float *)f, n, cnt);
+    if (fp64) k_set<double><<<grid, kBlock, 0, st>>>(src, (double *)f, n, offset, cnt);
+    else k_set<float><<<grid, kBlock, 0, st>>>(src, (float *)f, n, offset, cnt);
     return cudaGetLastError();
+}
+
+// Host side: f^eq and the domain check of the reference state are the device
+// formulas compiled for the host (they are __host__ __device__).
+// The kernels evaluate f^eq with the parameters rounded to their arithmetic
+// type, so the reference residual rdev = f^eq(ubar) - fbar must be taken with
+// those same rounded parameters: with the exact ones it would hold a constant
+// inconsistency (for shallow water (g - fl(g)) hbar^2 / (4V)) that the
+// relaxation re-injects at every stage.
+static ParamsR<double> kernel_params(const Params &P, bool fp64)
+{
+    ParamsR<double> d = params_as<double>(P);
+    if (fp64) return d;
+    const ParamsR<float> f = params_as<float>(P);
+    d.V = f.V;
+    d.inv2V = f.inv2V;
+    for (int j = 0; j < 2; ++j) {
+        d.a[j] = f.a[j];
+        d.c[j] = f.c[j];
+    }
+    d.g = f.g;
+    d.gamma_m1 = f.gamma_m1;
+    d.gV4 = f.gV4;
+    d.inv16gV = f.inv16gV;
+    return d;
+}
+
+template <class Sys>
+static bool reference_for(bool fp64, const double *u_ref, Params &P)
+{
+    constexpr int Q = Sys::Q, M = Sys::M;
+    P.shifted = 0;
+    const ParamsR<double> Pd = kernel_params(P, fp64);
+    double u[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int m = 0; m < M; ++m) {
+        u[m] = u_ref[m];
+        if (!std::isfinite(u[m])) return false;
+    }
+    if (!Sys::template admissible<double>(Pd, u)) return false;
+    auto storage = [fp64](double v) { return fp64 ? v : (double)(float)v; };
+    double feq[16];
+    Sys::template equilibrium<double>(Pd, u, feq);
+    for (int i = 0; i < 16; ++i) P.fbar[i] = i < Q * M ? storage(feq[i]) : 0.0;
+    double ub[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int m = 0; m < M; ++m) {
+        double s = 0.0;  // exact: a few values of the storage precision
+        for (int k = 0; k < Q; ++k) s += P.fbar[k * M + m];
+        ub[m] = storage(s);
+        P.ubar[m] = ub[m];
+        P.cm[m] = s - ub[m];
+    }
+    for (int m = M; m < 4; ++m) P.ubar[m] = P.cm[m] = 0.0;
+    if (!Sys::template admissible<double>(Pd, ub)) return false;
+    Sys::template equilibrium<double>(Pd, ub, feq);
+    for (int i = 0; i < 16; ++i) P.rdev[i] = i < Q * M ? feq[i] - P.fbar[i] : 0.0;
+    // reference velocity (and pressure) of the deviation forms, from the rounded ubar
+    for (int i = 0; i < 4; ++i) P.aux[i] = 0.0;
+    if (M >= 2) {
+        for (int j = 0; j + 1 < M && j < 2; ++j) P.aux[j] = ub[1 + j] / ub[0];
+        if (M == 4) P.aux[2] = Pd.gamma_m1 * (ub[3] - 0.5 * (ub[1] * P.aux[0] + ub[2] * P.aux[1]));
+    }
+    P.shifted = 1;
+    return true;
+}
+
+bool reference_state(int family, bool fp64, const double *u_ref, Params &P)
+{
+    switch (family) {
+    case FAM_LINEAR1: return reference_for<Scalar<1, false>>(fp64, u_ref, P);
+    case FAM_LINEAR2: return reference_for<Scalar<2, false>>(fp64, u_ref, P);
+    case FAM_BURGERS1: return reference_for<Scalar<1, true>>(fp64, u_ref, P);
+    case FAM_BURGERS2: return reference_for<Scalar<2, true>>(fp64, u_ref, P);
+    case FAM_SW1: return reference_for<ShallowWater<1>>(fp64, u_ref, P);
+    case FAM_SW2: return reference_for<ShallowWater<2>>(fp64, u_ref, P);
+    case FAM_EULER2: return reference_for<Euler2>(fp64, u_ref, P);
+    }
+    return false;
 }
 
 cudaError_t adjoint_scalar(int, bool, bool, const AdjointLaunch &);

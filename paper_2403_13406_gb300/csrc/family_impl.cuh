@@ -38,7 +38,12 @@ cudaError_t stage_family(bool fp64, bool entropic, bool diag, const StageLaunch 
 // Tile of the fused 1D kernel: about four resident blocks per SM over the grid
 // (a multiple of 32 cells), at least 128 cells, and a window that fits 96 KiB of
 // shared memory.
-inline int fused_tile(int64_t n, int halo, int bytes_per_cell)
+// Tile of the temporally blocked 1D kernel: enough tiles to give every SM
+// `bps` resident blocks in a single wave, with the window of a block taking
+// at most its share of the SM's shared memory.
+constexpr int kSmemPerSm = 220 * 1024;
+
+inline int fused_tile(int64_t n, int halo, int bytes_per_cell, int bps)
 {
     static int sms = 0;
     if (!sms) {
@@ -47,10 +52,10 @@ inline int fused_tile(int64_t n, int halo, int bytes_per_cell)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
     }
-    int64_t t = (n + 4 * sms - 1) / (4 * sms);
+    int64_t t = (n + (int64_t)bps * sms - 1) / ((int64_t)bps * sms);
     t = ((t + 31) / 32) * 32;
     if (t < 128) t = 128;
-    const int64_t tmax = (96 * 1024) / bytes_per_cell - 2 * halo;
+    const int64_t tmax = (kSmemPerSm / bps) / bytes_per_cell - 2 * halo;
     if (t > tmax) t = tmax;
     return (int)t;
 }
@@ -59,17 +64,20 @@ template <class Sys, class R, bool ENT>
 cudaError_t fused_one(const FusedLaunch &L)
 {
     constexpr int NP = Sys::Q * Sys::M;
-    const int tile = fused_tile(L.n, L.sl.halo, NP * (int)sizeof(R));
+    static int bps = 0;  // resident blocks per SM allowed by the registers (at most 4)
+    if (!bps) {
+        cudaFuncSetAttribute(k_step1d<Sys, R, ENT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPerSm);
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step1d<Sys, R, ENT>, kFusedBlock, 0) != cudaSuccess)
+            occ = 1;
+        bps = occ < 1 ? 1 : (occ > 4 ? 4 : occ);
+    }
+    const int tile = fused_tile(L.n, L.sl.halo, NP * (int)sizeof(R), bps);
     if (tile < 32) return cudaErrorInvalidValue;
     const size_t smem = (size_t)(tile + 2 * L.sl.halo) * NP * sizeof(R);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_step1d<Sys, R, ENT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024 + 64);
-        attr_set = true;
-    }
     FusedArgs<R> a{(const R *)L.fin, (R *)L.fout, L.n, tile, L.cnt};
     const unsigned grid = (unsigned)((L.n + tile - 1) / tile);
-    k_step1d<Sys, R, ENT><<<grid, kBlock, smem, L.stream>>>(a, L.sl, params_as<R>(L.P));
+    k_step1d<Sys, R, ENT><<<grid, kFusedBlock, smem, L.stream>>>(a, L.sl, params_as<R>(L.P));
     return cudaGetLastError();
 }
 

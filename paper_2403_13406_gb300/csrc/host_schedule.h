@@ -104,4 +104,24 @@ inline int64_t num_M(const eslbm_config &c)
     return 1;
 }
 
+// Kernel parameters of a configuration, with the reference equilibrium of the
+// shifted storage; ESLBM_ERR_DOMAIN if cfg.u_ref is outside the domain.
+inline eslbm_status params_of(const eslbm_config &c, Params &P)
+{
+    P = Params{};
+    P.V = c.V;
+    P.a[0] = c.a[0];
+    P.a[1] = c.a[1];
+    P.c[0] = c.c[0];
+    P.c[1] = c.c[1];
+    P.g = c.g;
+    P.gamma = c.gamma;
+    P.omega = c.omega;
+    P.t_max = c.t_max > 0.0 ? c.t_max : 3.0;
+    // quadratic kinetic entropies: the entropic omega is 2 exactly (Proposition 2)
+    if (c.omega_mode == ESLBM_OMEGA_ENTROPIC && c.system == ESLBM_LINEAR) P.omega = 2.0;
+    if (c.shifted && !reference_state(family_of(c), c.precision == ESLBM_FP64, c.u_ref, P)) return ESLBM_ERR_DOMAIN;
+    return ESLBM_OK;
+}
+
 }  // namespace eslbm

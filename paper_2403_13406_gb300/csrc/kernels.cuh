@@ -16,6 +16,7 @@ namespace cg = cooperative_groups;
 namespace eslbm {
 
 constexpr int kBlock = 256;       // threads per block of the per-cell kernels
+constexpr int kFusedBlock = 256;  // threads per block of the temporally blocked 1D kernel
 constexpr int kRedBlocks = 1024;  // fixed grid of the totals reduction (deterministic order)
 constexpr int kRedThreads = 256;
 
@@ -48,22 +49,46 @@ __device__ __forceinline__ void warp_count(bool flag, unsigned long long *counte
     if (mask && (threadIdx.x & 31) == 0) atomicAdd(counter, (unsigned long long)__popc(mask));
 }
 
+// Conserved moments u of the distributions held in f (f itself, or f - fbar in
+// the shifted storage) and the relaxation target tgt_k = f^eq_k(u) minus what
+// the storage subtracts, so that f^eq - f = tgt - (stored values) in both forms.
+template <class Sys, class R>
+__device__ __forceinline__ void moments_target(const ParamsR<R> &P, const R *f, R *u, R *tgt)
+{
+    constexpr int Q = Sys::Q, M = Sys::M;
+    R s[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        R a = f[m];
+#pragma unroll
+        for (int k = 1; k < Q; ++k) a += f[k * M + m];
+        s[m] = a;
+    }
+    if (!P.shifted) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) u[m] = s[m];
+        Sys::template equilibrium<R>(P, u, tgt);
+        return;
+    }
+    R du[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        du[m] = s[m] + P.cm[m];
+        u[m] = P.ubar[m] + du[m];
+    }
+    Sys::template equilibrium_dev<R>(P, du, u, tgt);
+#pragma unroll
+    for (int i = 0; i < Q * M; ++i) tgt[i] += P.rdev[i];
+}
+
 // One relaxation of one cell (eq. relaxationDiscretizationOmega), in place.
 template <class Sys, class R, bool ENTROPIC, bool DIAG>
 __device__ __forceinline__ void relax_cell(const ParamsR<R> &P, R *f, int kind, bool &fallback, bool &increase,
                                            R &omega_used)
 {
     constexpr int Q = Sys::Q, M = Sys::M;
-    R u[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-        R s = f[m];
-#pragma unroll
-        for (int k = 1; k < Q; ++k) s += f[k * M + m];
-        u[m] = s;
-    }
-    R feq[Q * M];
-    Sys::template equilibrium<R>(P, u, feq);
+    R u[M], feq[Q * M];
+    moments_target<Sys, R>(P, f, u, feq);
     fallback = false;
     increase = false;
     if (kind == KIND_PROJECT) {  // R_1: projection on the equilibrium (Section 6.1)
@@ -156,7 +181,8 @@ template <class R> struct FusedArgs {
 };
 
 template <class Sys, class R, bool ENTROPIC>
-__global__ void __launch_bounds__(kBlock) k_step1d(FusedArgs<R> a, StageList sl, ParamsR<R> P)
+__global__ void __launch_bounds__(kFusedBlock, sizeof(R) == 4 ? 4 : 2)
+    k_step1d(FusedArgs<R> a, StageList sl, ParamsR<R> P)
 {
     constexpr int Q = Sys::Q, M = Sys::M, NP = Q * M;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -240,14 +266,8 @@ template <class Sys, class R, bool ENTROPIC>
 __device__ __forceinline__ void relax_adjoint(const ParamsR<R> &P, const R *f, const R *gout, int kind, R *gin)
 {
     constexpr int Q = Sys::Q, M = Sys::M;
-    R u[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-        R s = f[m];
-#pragma unroll
-        for (int k = 1; k < Q; ++k) s += f[k * M + m];
-        u[m] = s;
-    }
+    R u[M], feq[Q * M];
+    moments_target<Sys, R>(P, f, u, feq);
     R E[Q * M * M];
     Sys::template equilibrium_jacobian<R>(P, u, E);
     R a[M];  // sum_k E_k^T g'_k
@@ -267,8 +287,7 @@ __device__ __forceinline__ void relax_adjoint(const ParamsR<R> &P, const R *f, c
             for (int n = 0; n < M; ++n) gin[k * M + n] = a[n];
         return;
     }
-    R feq[Q * M], delta[Q * M];
-    Sys::template equilibrium<R>(P, u, feq);
+    R delta[Q * M];
 #pragma unroll
     for (int i = 0; i < Q * M; ++i) delta[i] = feq[i] - f[i];
     R w = P.omega;
@@ -476,7 +495,7 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(const double *__restrict__ u
         double feq[Q * M];
         Sys::template equilibrium<double>(P, u, feq);
 #pragma unroll
-        for (int j = 0; j < Q * M; ++j) f[(int64_t)j * ncell + i] = R(feq[j]);
+        for (int j = 0; j < Q * M; ++j) f[(int64_t)j * ncell + i] = R(P.shifted ? feq[j] - P.fbar[j] : feq[j]);
     }
     warp_count(bad, &cnt->domain_violations);
     warp_count(nonfinite, &cnt->non_finite);
@@ -485,23 +504,28 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(const double *__restrict__ u
 // distributions from double planes (rounded to the storage precision)
 template <class R>
 __global__ void __launch_bounds__(kBlock) k_set(const double *__restrict__ src, R *__restrict__ f, int64_t n,
-                                                Counters *cnt)
+                                                double offset, Counters *cnt)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool nonfinite = false;
     if (i < n) {
         const double v = src[i];
         nonfinite = !isfinite(v);
-        f[i] = R(v);
+        f[i] = R(v - offset);
     }
     warp_count(nonfinite, &cnt->non_finite);
 }
 
 // Moments u_m = sum_k f_k,m, or the planes [p0, p0 + np) of the logical
-// distributions, as double planes (the pending shift sh is applied).
+// distributions, as double planes (the pending shift sh is applied; in the
+// shifted storage f = stored + fbar).
+struct RefPlanes {
+    double fbar[16];
+};
+
 template <int DIM, class R, bool MOMENTS>
 __global__ void __launch_bounds__(kBlock) k_gather(const R *__restrict__ f, double *__restrict__ out, int64_t nx,
-                                                   int64_t ny, int M, int p0, int np, Shift sh)
+                                                   int64_t ny, int M, int p0, int np, Shift sh, RefPlanes ref)
 {
     constexpr int Q = Lattice<DIM>::Q;
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -513,12 +537,13 @@ __global__ void __launch_bounds__(kBlock) k_gather(const R *__restrict__ f, doub
             double s = 0.0;
 #pragma unroll
             for (int k = 0; k < Q; ++k)
-                s += double(f[(int64_t)(k * M + m) * ncell + src_cell<DIM>(k, x, y, nx, ny, sh)]);
+                s += double(f[(int64_t)(k * M + m) * ncell + src_cell<DIM>(k, x, y, nx, ny, sh)]) + ref.fbar[k * M + m];
             out[(int64_t)m * ncell + o] = s;
         }
     } else {
         for (int p = p0; p < p0 + np; ++p)
-            out[(int64_t)(p - p0) * ncell + o] = double(f[(int64_t)p * ncell + src_cell<DIM>(p / M, x, y, nx, ny, sh)]);
+            out[(int64_t)(p - p0) * ncell + o] =
+                double(f[(int64_t)p * ncell + src_cell<DIM>(p / M, x, y, nx, ny, sh)]) + ref.fbar[p];
     }
 }
 
@@ -541,7 +566,7 @@ __global__ void __launch_bounds__(kRedThreads) k_totals_partial(const R *__restr
         for (int k = 0; k < Q; ++k) {
             const int64_t s = src_cell<DIM>(k, x, y, nx, ny, sh);
 #pragma unroll
-            for (int m = 0; m < M; ++m) fc[k * M + m] = double(f[(int64_t)(k * M + m) * ncell + s]);
+            for (int m = 0; m < M; ++m) fc[k * M + m] = double(f[(int64_t)(k * M + m) * ncell + s]) + P.fbar[k * M + m];
         }
 #pragma unroll
         for (int m = 0; m < M; ++m) {

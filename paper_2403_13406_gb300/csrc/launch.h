@@ -44,11 +44,17 @@ cudaError_t launch_init_eq(int family, bool fp64, const double *u0, void *f, int
 cudaError_t launch_totals(int family, bool fp64, const void *f, double *partials, double *out, int64_t nx,
                           int64_t ny, const Shift &sh, const Params &P, cudaStream_t st);
 // gathers (pending shift applied) and conversion
+// (fbar: the 16 reference distributions of the shifted storage, zeros otherwise)
 cudaError_t launch_gather_moments(int dim, bool fp64, const void *f, double *out, int64_t nx, int64_t ny, int M,
-                                  const Shift &sh, cudaStream_t st);
+                                  const Shift &sh, const double *fbar, cudaStream_t st);
 cudaError_t launch_gather_planes(int dim, bool fp64, const void *f, double *out, int64_t nx, int64_t ny, int M,
-                                 int plane0, int nplanes, const Shift &sh, cudaStream_t st);
-cudaError_t launch_set(bool fp64, const double *src, void *f, int64_t n, Counters *cnt, cudaStream_t st);
+                                 int plane0, int nplanes, const Shift &sh, const double *fbar, cudaStream_t st);
+// f = src - offset rounded to the storage precision
+cudaError_t launch_set(bool fp64, const double *src, void *f, int64_t n, double offset, Counters *cnt,
+                       cudaStream_t st);
+// Reference equilibrium of the shifted storage for u_ref (fills P.fbar, ubar, cm,
+// rdev for the storage precision); false if u_ref is outside the domain.
+bool reference_state(int family, bool fp64, const double *u_ref, Params &P);
 
 struct AdjointLaunch {
     const void *fin;   // forward input of the stage (physical layout)

@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "../../include/eslbm.h"
+#include "host_schedule.h"
 #include "launch.h"
 
 using namespace eslbm;
@@ -46,15 +47,6 @@ eslbm_status scratch_for_current_device(double **out)
     return ESLBM_OK;
 }
 
-int family_from(const eslbm_config &c)
-{
-    switch (c.system) {
-    case ESLBM_LINEAR: return c.dim == 1 ? FAM_LINEAR1 : FAM_LINEAR2;
-    case ESLBM_BURGERS: return c.dim == 1 ? FAM_BURGERS1 : FAM_BURGERS2;
-    case ESLBM_SHALLOW_WATER: return c.dim == 1 ? FAM_SW1 : FAM_SW2;
-    default: return FAM_EULER2;
-    }
-}
 
 }  // namespace
 
@@ -72,15 +64,7 @@ extern "C" eslbm_status eslbm_read_totals_noalloc(const eslbm_config *cfg, const
     if (s != ESLBM_OK) return s;
 
     Params P;
-    P.V = cfg->V;
-    P.a[0] = cfg->a[0];
-    P.a[1] = cfg->a[1];
-    P.c[0] = cfg->c[0];
-    P.c[1] = cfg->c[1];
-    P.g = cfg->g;
-    P.gamma = cfg->gamma;
-    P.omega = cfg->omega;
-    P.t_max = cfg->t_max > 0.0 ? cfg->t_max : 3.0;
+    if ((s = params_of(*cfg, P)) != ESLBM_OK) return s;  // the reference of the shifted storage
     // pull offsets of T(pending_shift): population k at x reads x - sign_k * shift
     Shift sh;
     for (int k = 0; k < 4; ++k) sh.roff[k] = 0;
@@ -98,7 +82,7 @@ extern "C" eslbm_status eslbm_read_totals_noalloc(const eslbm_config *cfg, const
     double *dst = out_on_device ? out : final_totals;
     // every block writes all of its partial sums and the final pass overwrites the totals,
     // so nothing in the scratch has to start at zero
-    if (launch_totals(family_from(*cfg), cfg->precision == ESLBM_FP64, f, partials, dst, cfg->nx, cfg->ny, sh, P,
+    if (launch_totals(family_of(*cfg), cfg->precision == ESLBM_FP64, f, partials, dst, cfg->nx, cfg->ny, sh, P,
                       st) != cudaSuccess)
         return ESLBM_ERR_CUDA;
     if (!out_on_device) {

@@ -41,12 +41,12 @@ template <int DIM, bool BURGERS> struct Scalar {
     static constexpr int M = 1;
     static constexpr bool LINEAR = !BURGERS;
 
-    template <class R> __device__ static R flux(const ParamsR<R> &P, int j, R u)
+    template <class R> __host__ __device__ static R flux(const ParamsR<R> &P, int j, R u)
     {
         return BURGERS ? P.c[j] * R(0.5) * u * u : P.a[j] * u;
     }
 
-    template <class R> __device__ static void equilibrium(const ParamsR<R> &P, const R *u, R *feq)
+    template <class R> __host__ __device__ static void equilibrium(const ParamsR<R> &P, const R *u, R *feq)
     {
         const R inv2V = P.inv2V;
         const R phi0 = flux<R>(P, 0, u[0]);
@@ -56,6 +56,22 @@ template <int DIM, bool BURGERS> struct Scalar {
         for (int k = 0; k < Q; ++k) {
             const R phi = Lattice<DIM>::axis(k) == 0 ? phi0 : phi1;
             feq[k] = Lattice<DIM>::sign(k) > 0 ? base + phi * inv2V : base - phi * inv2V;
+        }
+    }
+
+    // f^eq_k(ubar + du) - f^eq_k(ubar) (u = ubar + du) without cancellation:
+    // phi(u) - phi(ubar) = c du (u + ubar) / 2 (Burgers), a du (linear)
+    template <class R> __device__ static void equilibrium_dev(const ParamsR<R> &P, const R *du, const R *u, R *fd)
+    {
+        const R inv2V = P.inv2V;
+        R dphi[2];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) dphi[j] = BURGERS ? P.c[j] * R(0.5) * du[0] * (u[0] + P.ubar[0]) : P.a[j] * du[0];
+        const R base = du[0] / R(Q);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const R dp = dphi[Lattice<DIM>::axis(k)];
+            fd[k] = Lattice<DIM>::sign(k) > 0 ? base + dp * inv2V : base - dp * inv2V;
         }
     }
 
@@ -71,7 +87,7 @@ template <int DIM, bool BURGERS> struct Scalar {
         }
     }
 
-    template <class R> __device__ static bool admissible(const ParamsR<R> &P, const R *u)
+    template <class R> __host__ __device__ static bool admissible(const ParamsR<R> &P, const R *u)
     {
 #pragma unroll
         for (int j = 0; j < DIM; ++j) {
@@ -104,8 +120,9 @@ template <int DIM, bool BURGERS> struct Scalar {
 
     // B = sum_k B_k(t delta_k), dB = d B / dt, and (if Dout) Delta_k = p - p'_k.
     // false outside the convexity domain.
-    template <class R> __device__ static bool eval(const ParamsR<R> &, const Ctx<R> &cx, R t, R &B, R &dB,
-                                                   R *Dout = nullptr)
+    template <class R, int WARM = 0>
+    __device__ static bool eval(const ParamsR<R> &, const Ctx<R> &cx, R t, R &B, R &dB, R *Dout = nullptr,
+                                R * = nullptr)
     {
         B = R(0);
         dB = R(0);
@@ -147,7 +164,7 @@ template <int DIM> struct ShallowWater {
     static constexpr int M = DIM + 1;
     static constexpr bool LINEAR = false;
 
-    template <class R> __device__ static void equilibrium(const ParamsR<R> &P, const R *u, R *feq)
+    template <class R> __host__ __device__ static void equilibrium(const ParamsR<R> &P, const R *u, R *feq)
     {
         const R h = u[0];
         const R g = P.g;
@@ -172,6 +189,43 @@ template <int DIM> struct ShallowWater {
             for (int m = 0; m < M; ++m) {
                 const R base = u[m] / R(Q);
                 feq[k * M + m] = plus ? base + phi[j][m] * inv2V : base - phi[j][m] * inv2V;
+            }
+        }
+    }
+
+    // f^eq_k(ubar + du) - f^eq_k(ubar) (u = ubar + du) without cancellation: with
+    // v = q / h, dv = v - vbar = (dq - vbar dh) / h, q_a v_b - qbar_a vbar_b = dq_a v_b + qbar_a dv_b
+    // and g h^2 / 2 - g hbar^2 / 2 = g dh (h + hbar) / 2
+    // (P.aux[j] = vbar_j, the reference velocity)
+    template <class R> __device__ static void equilibrium_dev(const ParamsR<R> &P, const R *du, const R *u, R *fd)
+    {
+        const R h = u[0], hb = P.ubar[0], dh = du[0];
+        const R rh = R(1) / h;
+        R v[2], dv[2];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+            v[j] = u[1 + j] * rh;
+            dv[j] = (du[1 + j] - P.aux[j] * dh) * rh;
+        }
+        const R dhp = R(0.5) * P.g * dh * (h + hb);
+        R dphi[2][3];
+        dphi[0][0] = du[1];
+        dphi[0][1] = du[1] * v[0] + P.ubar[1] * dv[0] + dhp;
+        if (DIM == 2) {
+            dphi[0][2] = du[2] * v[0] + P.ubar[2] * dv[0];
+            dphi[1][0] = du[2];
+            dphi[1][1] = du[1] * v[1] + P.ubar[1] * dv[1];
+            dphi[1][2] = du[2] * v[1] + P.ubar[2] * dv[1] + dhp;
+        }
+        const R inv2V = P.inv2V;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int j = Lattice<DIM>::axis(k);
+            const bool plus = Lattice<DIM>::sign(k) > 0;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const R base = du[m] / R(Q);
+                fd[k * M + m] = plus ? base + dphi[j][m] * inv2V : base - dphi[j][m] * inv2V;
             }
         }
     }
@@ -206,7 +260,7 @@ template <int DIM> struct ShallowWater {
     }
 
     // h > 0 and |v_j| + sqrt(g h) < 2V/Q along each axis (Example 3)
-    template <class R> __device__ static bool admissible(const ParamsR<R> &P, const R *u)
+    template <class R> __host__ __device__ static bool admissible(const ParamsR<R> &P, const R *u)
     {
         const R h = u[0];
         if (!(h > R(0)) || !isfinite(h)) return false;
@@ -256,10 +310,17 @@ template <int DIM> struct ShallowWater {
         }
     }
 
-    template <class R> __device__ static bool eval(const ParamsR<R> &P, const Ctx<R> &cx, R t, R &B, R &dB,
-                                                   R *Dout = nullptr)
+    // WARM (FP32 only): 0 = start from the linearised guess b = t beta_1; 1 = t is +1 and bio[0..Q)
+    // holds b(-1): start from b(-1) + 2 beta_1; 2 = bio holds b(-1) and b(+1): start from the cubic
+    // t beta_1 + t^2 beta_2 + t^3 beta_3 through them.  b(t) is odd-plus-even smooth in t with
+    // b'(0) = beta_1, so these guesses are off by O(|delta|^3) and O(|delta|^4), and one Newton step
+    // brings them to the rounding level.  The solution is stored in bio[Q * (t > 0) + k] when bio is set.
+    template <class R, int WARM = 0>
+    __device__ static bool eval(const ParamsR<R> &P, const Ctx<R> &cx, R t, R &B, R &dB, R *Dout = nullptr,
+                                R *bio = nullptr)
     {
         constexpr bool FAST = sizeof(R) == 4;
+        constexpr int warm = FAST ? WARM : 0;
         const R gV4 = P.gV4;
         const R inv16gV = P.inv16gV;
         const R W = cx.W;
@@ -280,6 +341,17 @@ template <int DIM> struct ShallowWater {
             b[k] = (r[k] - lin) * cx.rg0[k];
             bscale[k] = (fabs(r[k]) + fabs(lin)) * fabs(cx.rg0[k]);
             db[k] = R(0);
+            if constexpr (warm != 0) {
+                const R beta1 = ((cx.d[k][1 + dax] - cx.v[dax] * cx.d[k][0]) -
+                                 R(0.5) * sg * W * cx.d[k][0] * cx.rc[k]) * cx.rg0[k];
+                if constexpr (warm == 1) {
+                    b[k] = bio[k] + R(2) * beta1;
+                } else {
+                    const R beta2 = R(0.5) * (bio[Q + k] + bio[k]);
+                    const R beta3 = R(0.5) * (bio[Q + k] - bio[k]) - beta1;
+                    b[k] = t * (beta1 + t * (beta2 + t * beta3));
+                }
+            }
         }
         // one Newton step on G(b) = -b f'_1 - sign dW (2W - dW)/(16 g V) - r for population k
         auto newton = [&](int k) {
@@ -296,15 +368,20 @@ template <int DIM> struct ShallowWater {
         };
         // min_inner steps for every population, in lockstep: straight-line code that the
         // scheduler can interleave across populations, and no divergence for smooth cells
-#pragma unroll
-        for (int it = 0; it < Tol<R>::min_inner; ++it)
+        if constexpr (warm != 0) {
 #pragma unroll
             for (int k = 0; k < Q; ++k) newton(k);
+        } else {
+#pragma unroll
+            for (int it = 0; it < Tol<R>::min_inner; ++it)
+#pragma unroll
+                for (int k = 0; k < Q; ++k) newton(k);
+        }
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             R prev = fabs(db[k]);
             bool conv = prev <= Tol<R>::inner * (fabs(b[k]) + bscale[k]);
-            for (int it = Tol<R>::min_inner; !conv && it < Tol<R>::max_inner; ++it) {
+            for (int it = warm ? 1 : Tol<R>::min_inner; !conv && it < Tol<R>::max_inner; ++it) {
                 newton(k);
                 const R ad = fabs(db[k]);
                 if (ad <= Tol<R>::inner * (fabs(b[k]) + bscale[k])) {
@@ -315,7 +392,9 @@ template <int DIM> struct ShallowWater {
                 }
                 prev = ad;
             }
-            if (FAST && !conv) conv = fabs(db[k]) <= Tol<R>::inner_accept * (fabs(b[k]) + bscale[k]);
+            // out of iterations while the steps hover at the rounding level (they need not grow, so
+            // the stall test above may not fire): accept as at a stall
+            if (!conv) conv = fabs(db[k]) <= Tol<R>::inner_accept * (fabs(b[k]) + bscale[k]);
             good &= conv;
         }
         B = R(0);
@@ -344,6 +423,8 @@ template <int DIM> struct ShallowWater {
                 Dout[k * M + 1 + dax] = bk;
                 if (DIM == 2) Dout[k * M + 2 - dax] = ct;
             }
+            if constexpr (FAST && warm < 2)
+                if (bio) bio[warm * Q + k] = bk;  // b(-1) (warm 0) or b(+1) (warm 1)
         }
         return good;
     }
@@ -359,7 +440,7 @@ struct Euler2 {
     static constexpr int M = 4;
     static constexpr bool LINEAR = false;
 
-    template <class R> __device__ static void equilibrium(const ParamsR<R> &P, const R *u, R *feq)
+    template <class R> __host__ __device__ static void equilibrium(const ParamsR<R> &P, const R *u, R *feq)
     {
         const R rho = u[0], mx = u[1], my = u[2], E = u[3];
         const R vx = mx / rho, vy = my / rho;
@@ -375,6 +456,39 @@ struct Euler2 {
             for (int m = 0; m < 4; ++m) {
                 const R base = u[m] * R(0.25);
                 feq[k * 4 + m] = plus ? base + phi[m] * inv2V : base - phi[m] * inv2V;
+            }
+        }
+    }
+
+    // f^eq_k(ubar + du) - f^eq_k(ubar) (u = ubar + du) without cancellation: with
+    // v = m / rho, dv = (dm - vbar drho) / rho, m_a v_b - mbar_a vbar_b = dm_a v_b + mbar_a dv_b,
+    // dp = (gamma - 1)(dE - (dm.v + mbar.dv) / 2) and
+    // v_a (E + p) - vbar_a (Ebar + pbar) = dv_a (E + p) + vbar_a (dE + dp)
+    // (P.aux = (vbar_x, vbar_y, pbar), the reference velocity and pressure)
+    template <class R> __device__ static void equilibrium_dev(const ParamsR<R> &P, const R *du, const R *u, R *fd)
+    {
+        const R rho = u[0], rr = R(1) / u[0];
+        const R vx = u[1] * rr, vy = u[2] * rr;
+        const R vbx = P.aux[0], vby = P.aux[1];
+        const R dvx = (du[1] - vbx * du[0]) * rr, dvy = (du[2] - vby * du[0]) * rr;
+        const R pb = P.aux[2];
+        const R dK = R(0.5) * (du[1] * vx + du[2] * vy + P.ubar[1] * dvx + P.ubar[2] * dvy);
+        const R dp = P.gamma_m1 * (du[3] - dK);
+        const R Ep = u[3] + pb + dp;
+        (void)rho;
+        const R dphx[4] = {du[1], du[1] * vx + P.ubar[1] * dvx + dp, du[2] * vx + P.ubar[2] * dvx,
+                           dvx * Ep + vbx * (du[3] + dp)};
+        const R dphy[4] = {du[2], du[1] * vy + P.ubar[1] * dvy, du[2] * vy + P.ubar[2] * dvy + dp,
+                           dvy * Ep + vby * (du[3] + dp)};
+        const R inv2V = P.inv2V;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const R *dphi = (k & 1) ? dphy : dphx;
+            const bool plus = k < 2;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const R base = du[m] * R(0.25);
+                fd[k * 4 + m] = plus ? base + dphi[m] * inv2V : base - dphi[m] * inv2V;
             }
         }
     }
@@ -410,7 +524,7 @@ struct Euler2 {
         }
     }
 
-    template <class R> __device__ static bool admissible(const ParamsR<R> &P, const R *u)
+    template <class R> __host__ __device__ static bool admissible(const ParamsR<R> &P, const R *u)
     {
         const R rho = u[0];
         if (!(rho > R(0))) return false;
@@ -424,8 +538,8 @@ struct Euler2 {
         R unused;
     };
     template <class R> __device__ static void prepare(const ParamsR<R> &, const R *, const R *, Ctx<R> &) {}
-    template <class R> __device__ static bool eval(const ParamsR<R> &, const Ctx<R> &, R, R &B, R &dB,
-                                                   R * = nullptr)
+    template <class R, int WARM = 0>
+    __device__ static bool eval(const ParamsR<R> &, const Ctx<R> &, R, R &B, R &dB, R * = nullptr, R * = nullptr)
     {
         B = R(NAN);
         dB = R(NAN);
@@ -446,7 +560,9 @@ struct Euler2 {
 //     above the root).  FP32 stops after the first exact evaluation at the
 //     model root (its O(|delta|^3) error is below the storage rounding of
 //     omega delta); FP64 iterates to a relative step of 1e-9 and evaluates once
-//     more.
+//     more.  In FP32 the inner solves of the evaluation at +1 and of the later
+//     ones start from the deviations already found at -1 (and +1), which
+//     leaves one inner Newton step to do instead of two.
 //  4. Return the chord root of the final bracket: for a convex F it never
 //     exceeds t*, so the cell's microscopic entropy does not increase.  If
 //     Newton converged from below (every evaluation <= 0 at rounding level),
@@ -459,7 +575,9 @@ __device__ R entropic_omega(const ParamsR<R> &P, const typename Sys::template Ct
 {
     fallback = false;
     R Em, dEm;
-    if (!Sys::template eval<R>(P, cx, R(-1), Em, dEm)) {
+    R bw[2 * Sys::Q];  // deviations at t = -1 and t = +1: warm starts of the later evaluations
+    bool warm2 = false;
+    if (!Sys::template eval<R, 0>(P, cx, R(-1), Em, dEm, nullptr, bw)) {
         fallback = true;
         return R(1);
     }
@@ -470,7 +588,8 @@ __device__ R entropic_omega(const ParamsR<R> &P, const typename Sys::template Ct
     R t;
     bool last = false, last_newton = false;
     R Bp, dBp;
-    if (R(1) < hi && Sys::template eval<R>(P, cx, R(1), Bp, dBp)) {
+    if (R(1) < hi && Sys::template eval<R, 1>(P, cx, R(1), Bp, dBp, nullptr, bw)) {
+        warm2 = true;
         const R F1 = Bp - Em;
         if (F1 == R(0)) return R(2);
         if (F1 < R(0)) {
@@ -487,7 +606,7 @@ __device__ R entropic_omega(const ParamsR<R> &P, const typename Sys::template Ct
         const R b2 = R(0.5) * (Bp + Em) - b4;
         R tm = R(1);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 3; ++i) {
             const R m = tm * tm * (b2 + tm * (b3 + tm * b4)) - Em;
             const R dm = tm * (R(2) * b2 + tm * (R(3) * b3 + R(4) * b4 * tm));
             tm -= qdiv(m, dm);
@@ -496,6 +615,13 @@ __device__ R entropic_omega(const ParamsR<R> &P, const typename Sys::template Ct
             t = tm;
             last = sizeof(R) == 4;  // FP32: one exact evaluation at the model root
             last_newton = true;
+        } else if (sizeof(R) == 4) {
+            // FP32, model root on the wrong side of t = 1: F(1) is then at the rounding level
+            // of B (the odd part of B(t) is O(|delta|^3), below FP32 resolution for small
+            // deviations), and iterating on such values would only chase noise.  Take what the
+            // two evaluations bracket: F(1) <= 0 allows omega = 2; F(1) > 0 gives the chord
+            // through F(0) = -E0 and F(1), which does not exceed the root of a convex F.
+            return F1 < R(0) ? R(2) : R(1) + Em / Bp;
         } else {
             const R tn = R(1) - F1 / dBp;
             t = (dBp > R(0) && tn > lo && tn < hi) ? tn : R(0.5) * (lo + hi);
@@ -506,7 +632,8 @@ __device__ R entropic_omega(const ParamsR<R> &P, const typename Sys::template Ct
     }
     for (int it = 0; it < Tol<R>::max_outer; ++it) {
         R F, dF;
-        const bool ok = Sys::template eval<R>(P, cx, t, F, dF);
+        const bool ok = warm2 ? Sys::template eval<R, 2>(P, cx, t, F, dF, nullptr, bw)
+                              : Sys::template eval<R, 0>(P, cx, t, F, dF);
         if (ok) F -= Em;
         if (ok && F <= R(0)) {
             lo = t;

@@ -39,7 +39,7 @@ class Config(ctypes.Structure):
                 ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("V", ctypes.c_double),
                 ("omega", ctypes.c_double), ("a", ctypes.c_double * 2), ("c", ctypes.c_double * 2),
                 ("g", ctypes.c_double), ("gamma", ctypes.c_double), ("t_max", ctypes.c_double),
-                ("diagnostics", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("diagnostics", ctypes.c_int32), ("shifted", ctypes.c_int32), ("u_ref", ctypes.c_double * 4)]
 
 
 class Sizes(ctypes.Structure):
@@ -131,7 +131,8 @@ class EslbmError(RuntimeError):
 
 
 def make_config(dim, system, nx, ny=1, V=1.0, precision="fp32", omega_mode="fixed", omega=2.0, scheme="I",
-                a=(0.0, 0.0), c=(1.0, 1.0), g=1.0, gamma=1.4, t_max=3.0, kappa=1, diagnostics=False):
+                a=(0.0, 0.0), c=(1.0, 1.0), g=1.0, gamma=1.4, t_max=3.0, kappa=1, diagnostics=False, u_ref=None):
+    """Configuration of one lattice; u_ref (conserved values) selects the shifted storage."""
     cfg = Config()
     cfg.dim = int(dim)
     cfg.system = SYSTEMS[system] if isinstance(system, str) else int(system)
@@ -149,6 +150,10 @@ def make_config(dim, system, nx, ny=1, V=1.0, precision="fp32", omega_mode="fixe
     cfg.gamma = float(gamma)
     cfg.t_max = float(t_max)
     cfg.diagnostics = 1 if diagnostics else 0
+    cfg.shifted = 0 if u_ref is None else 1
+    if u_ref is not None:
+        for i, v in enumerate(u_ref):
+            cfg.u_ref[i] = float(v)
     return cfg
 
 

@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_abi_version_and_status_strings(L):
-    assert L.eslbm_abi_version() == 1
+    assert L.eslbm_abi_version() == 2
     for s in (0, 1, 2, 3, 4, 5, 100, 77):
         assert L.eslbm_status_string(s)
 
@@ -70,12 +70,26 @@ def test_query_sizes(L):
     (dict(kappa=0), eslbm.ERR_ARG),
     (dict(system="sw", g=0.0), eslbm.ERR_ARG),
     (dict(system="linear", a=(1.6, 0.0)), eslbm.ERR_DOMAIN),
+    (dict(system="sw", V=4.0, g=9.81, u_ref=(-1.0, 0.0)), eslbm.ERR_DOMAIN),  # negative reference depth
+    (dict(system="sw", V=4.0, g=9.81, u_ref=(1.0, 5.0)), eslbm.ERR_DOMAIN),   # |v| + sqrt(g h) > V
+    (dict(system="burgers", V=1.0, u_ref=(1.2,)), eslbm.ERR_DOMAIN),          # |u| >= V (D1Q2)
 ])
 def test_query_rejects(L, bad, status):
     cfg = q(**bad)
     with pytest.raises(eslbm.EslbmError) as e:
         eslbm.query(cfg)
     assert e.value.status == status
+
+
+def test_shifted_reference_is_accepted(L):
+    """The reference state of the shifted storage is checked on the host at query time."""
+    assert eslbm.query(q(system="sw", V=4.0, g=9.81, u_ref=(1.0, 0.0))).planes == 4
+    assert eslbm.query(eslbm.make_config(2, "euler", 16, 16, V=8.0, u_ref=(1.0, 1.0, 1.0, 3.5))).planes == 16
+    bad = q(system="sw", V=4.0, g=9.81, u_ref=(1.0, 0.0))
+    bad.shifted = 2
+    with pytest.raises(eslbm.EslbmError) as e:
+        eslbm.query(bad)
+    assert e.value.status == eslbm.ERR_ARG
 
 
 def test_entropic_euler_is_unsupported(L):
