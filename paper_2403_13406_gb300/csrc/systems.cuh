@@ -562,7 +562,10 @@ struct Euler2 {
 //     omega delta); FP64 iterates to a relative step of 1e-9 and evaluates once
 //     more.  In FP32 the inner solves of the evaluation at +1 and of the later
 //     ones start from the deviations already found at -1 (and +1), which
-//     leaves one inner Newton step to do instead of two.
+//     leaves one inner Newton step to do instead of two; and when the spare
+//     datum of the model certifies it to the rounding level (smooth data), the
+//     model root itself is returned, lowered by the error bound, without the
+//     evaluation at it.
 //  4. Return the chord root of the final bracket: for a convex F it never
 //     exceeds t*, so the cell's microscopic entropy does not increase.  If
 //     Newton converged from below (every evaluation <= 0 at rounding level),
@@ -612,6 +615,21 @@ __device__ R entropic_omega(const ParamsR<R> &P, const typename Sys::template Ct
             tm -= qdiv(m, dm);
         }
         if (tm > lo && tm < hi) {
+            if (sizeof(R) == 4 && fabs(tm - R(1)) <= R(0.25)) {
+                // FP32: the four values fix the quartic model with one datum to spare.  Its
+                // residual r = (B'(1) + B'(-1)) - 3 (B(1) - B(-1)) is 4 c5 + 14 c7 + ... for
+                // B(t) = sum_n c_n t^n, the odd content the model misses (the even content
+                // vanishes at t = 1 in F).  When r is at the rounding level of B the model root
+                // is as good as an exact evaluation at it would certify: return it, lowered by
+                // the model's error bound over F'(tm) so that F stays <= 0.
+                const R r = (dBp + dEm) - R(3) * (Bp - Em);
+                const R tol = R(64) * R(1.1920929e-7) * (Bp + Em);
+                const R dm = tm * (R(2) * b2 + tm * (R(3) * b3 + R(4) * b4 * tm));
+                if (fabs(r) <= tol && dm > R(0)) {
+                    const R tc = tm - qdiv(fabs(r) + tol, dm);
+                    return R(1) + (tc > R(0) ? tc : R(0));
+                }
+            }
             t = tm;
             last = sizeof(R) == 4;  // FP32: one exact evaluation at the model root
             last_newton = true;
