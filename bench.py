@@ -40,10 +40,13 @@ BATCH_V = 8.0  # lattice velocity of the batched 2D shallow-water instances: sqr
 L2_FLUSH_BYTES = 512 << 20
 # FP32 roofline of the dominant kernel (the fused composite step k_step1d, entropic shallow water):
 # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz; and the FP32 operations of one cell-stage
-# (FADD + FMUL + 2 FFMA counted by ncu on this workload: 12.5e9 flops per launch over
-# 607 blocks x 1800 window cells x 18 stages)
+# (FADD + FMUL + 2 FFMA counted by ncu on this workload: 8.49e9 flops per launch over 607 blocks x
+# 1800 window cells x 18 stages).  The kernel is bound by instruction issue: 669 thread instructions
+# per cell-stage against 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FLOPS_PER_CELL_STAGE = 636.0
+FLOPS_PER_CELL_STAGE = 432.0
+ISSUE_PEAK_TINST = 152 * 4 * 32 * 2.07e9 / 1e12
+INST_PER_CELL_STAGE = 669.0
 
 
 def parse():
@@ -265,12 +268,16 @@ def main():
     achieved = flops / launch_s / 1e12
     peak, peak_kind = peaks()
     hbm_bytes = 2 * int(sim.sizes.planes) * N * 4
+    inst_rate = INST_PER_CELL_STAGE * N * int(sim.sizes.stages_per_step) / launch_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": 16.8e6,
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": 16.81e6,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                 "kernel": "k_step1d<ShallowWater<1>, float, entropic> (one composite step per launch)",
                 "launch_us": launch_s * 1e6, "stage_us": stage_s * 1e6,
                 "flops_per_cell_stage": FLOPS_PER_CELL_STAGE,
+                "issue_view": {"inst_per_cell_stage": INST_PER_CELL_STAGE, "achieved_tinst_s": inst_rate,
+                               "peak_tinst_s": ISSUE_PEAK_TINST, "frac": inst_rate / ISSUE_PEAK_TINST,
+                               "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2.07 GHz"},
                 "hbm_view": {"bytes_per_launch": hbm_bytes, "achieved_gbs": hbm_bytes / launch_s / 1e9,
                              "peak_gbs": peak, "frac": hbm_bytes / launch_s / 1e9 / peak,
                              "per_stage_model_gbs": 18 * hbm_bytes / launch_s / 1e9,
