@@ -200,7 +200,7 @@ template <int DIM> struct ShallowWater {
     template <class R> __device__ static void equilibrium_dev(const ParamsR<R> &P, const R *du, const R *u, R *fd)
     {
         const R h = u[0], hb = P.ubar[0], dh = du[0];
-        const R rh = R(1) / h;
+        const R rh = qdiv(R(1), h);
         R v[2], dv[2];
 #pragma unroll
         for (int j = 0; j < DIM; ++j) {
@@ -291,7 +291,7 @@ template <int DIM> struct ShallowWater {
     {
         const R h = u[0];
         cx.W = R(2) * P.g * h;
-        const R rh = R(1) / h;
+        const R rh = qdiv(R(1), h);
 #pragma unroll
         for (int j = 0; j < DIM; ++j) cx.v[j] = u[1 + j] * rh;
         const R nu = R(2) * P.V / R(Q);
@@ -341,10 +341,18 @@ template <int DIM> struct ShallowWater {
             b[k] = (r[k] - lin) * cx.rg0[k];
             bscale[k] = (fabs(r[k]) + fabs(lin)) * fabs(cx.rg0[k]);
             db[k] = R(0);
-            if constexpr (warm != 0) {
+            if constexpr (FAST) {
                 const R beta1 = ((cx.d[k][1 + dax] - cx.v[dax] * cx.d[k][0]) -
                                  R(0.5) * sg * W * cx.d[k][0] * cx.rc[k]) * cx.rg0[k];
-                if constexpr (warm == 1) {
+                if constexpr (warm == 0) {
+                    // second-order guess b = t beta_1 + t^2 beta_2 from the expansion of G(b(t)) = 0:
+                    // with K = 4 g V d_1 + sign W beta_1 the t^2 terms give
+                    // beta_2 = (d_1 beta_1 - (2 W beta_1 + sign K) K / (16 g V c^2)) / (W^2/(8gVc) - f_1)
+                    const R K = gV4 * cx.d[k][0] + sg * W * beta1;
+                    const R beta2 = (cx.d[k][0] * beta1 -
+                                     (R(2) * W * beta1 + sg * K) * K * inv16gV * cx.rc[k] * cx.rc[k]) * cx.rg0[k];
+                    b[k] = t * (beta1 + t * beta2);
+                } else if constexpr (warm == 1) {
                     b[k] = bio[k] + R(2) * beta1;
                 } else {
                     const R beta2 = R(0.5) * (bio[Q + k] + bio[k]);
@@ -368,7 +376,7 @@ template <int DIM> struct ShallowWater {
         };
         // min_inner steps for every population, in lockstep: straight-line code that the
         // scheduler can interleave across populations, and no divergence for smooth cells
-        if constexpr (warm != 0) {
+        if constexpr (FAST) {  // second-order or warm guesses: one step, more only if the check asks
 #pragma unroll
             for (int k = 0; k < Q; ++k) newton(k);
         } else {
@@ -381,7 +389,7 @@ template <int DIM> struct ShallowWater {
         for (int k = 0; k < Q; ++k) {
             R prev = fabs(db[k]);
             bool conv = prev <= Tol<R>::inner * (fabs(b[k]) + bscale[k]);
-            for (int it = warm ? 1 : Tol<R>::min_inner; !conv && it < Tol<R>::max_inner; ++it) {
+            for (int it = FAST ? 1 : Tol<R>::min_inner; !conv && it < Tol<R>::max_inner; ++it) {
                 newton(k);
                 const R ad = fabs(db[k]);
                 if (ad <= Tol<R>::inner * (fabs(b[k]) + bscale[k])) {
