@@ -117,7 +117,8 @@ struct Counters {
     unsigned int omega_max_bits;
     unsigned long long domain_violations;
     unsigned long long non_finite;
-    unsigned long long pad[3];
+    unsigned long long copy_timeouts;  // bulk-copy waits that gave up (never expected; reported as an error)
+    unsigned long long pad[2];
 };
 
 template <class R> struct Tol;

@@ -9,6 +9,24 @@ namespace eslbm {
 template <class Sys, int DIM, class R, bool ENT, bool DIAG>
 cudaError_t stage_one(const StageLaunch &L)
 {
+    constexpr int V4 = 16 / (int)sizeof(R);
+    if constexpr (DIM == 2 && !DIAG) {
+        // rows start on 16-byte boundaries: stage the pulled rows with bulk copies
+        if (L.nx % V4 == 0 && ((uintptr_t)L.fin & 15u) == 0) {
+            constexpr int NP = Sys::Q * Sys::M;
+            BulkArgs<R> b{(const R *)L.fin, (R *)L.fout, L.nx, L.ny, L.ncell, L.sh, L.kind, kRowTile + 2 * V4, L.cnt};
+            const size_t smem = 128 + (size_t)NP * (size_t)b.slot * sizeof(R);
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(k_stage_bulk<Sys, R, ENT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(128 + 16 * (kRowTile + 4) * sizeof(double)));
+                attr = true;
+            }
+            dim3 grid((unsigned)((L.nx + kRowTile - 1) / kRowTile), (unsigned)L.ny);
+            k_stage_bulk<Sys, R, ENT><<<grid, kRowThreads, smem, L.stream>>>(b, params_as<R>(L.P));
+            return cudaGetLastError();
+        }
+    }
     StageArgs<R> a{(const R *)L.fin, (R *)L.fout, L.nx, L.ny, L.ncell, L.sh, L.kind, L.cnt};
     dim3 grid((unsigned)((L.nx + kBlock - 1) / kBlock), (unsigned)L.ny);
     k_stage<Sys, DIM, R, ENT, DIAG><<<grid, kBlock, 0, L.stream>>>(a, params_as<R>(L.P));

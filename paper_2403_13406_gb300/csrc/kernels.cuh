@@ -160,6 +160,134 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageArgs<R> a, ParamsR<R> P)
 }
 
 // ---------------------------------------------------------------------------
+// 2D fused stage with the pulled rows staged in shared memory by bulk copies
+// (cp.async.bulk, completion counted on an mbarrier).  A block of 256 threads
+// owns a row segment [x0, x0 + T) of row y, T <= 1024 cells (four per thread:
+// with 4-plane states a block then keeps 16 KB of copies in flight, and enough
+// blocks fit on an SM to cover the memory latency).  For every plane the source
+// of the pull is one contiguous run of a single row: the same columns of row
+// y + roff (vertical populations) or columns x0 + roff ... of row y, wrapping
+// at the row end (horizontal populations).  Each run is copied from its 16-byte
+// boundary (rounded down; the remainder becomes an offset into the plane's
+// slot) as one or, when it wraps, two bulk copies; rows start on 16-byte
+// boundaries because the launcher requires nx to be a multiple of
+// 16 / sizeof(R).  One elected thread issues every copy; the block waits on the
+// mbarrier with a bounded number of polls, and on time-out counts the event and
+// skips the stage's arithmetic (the host reports it as an error).
+// ---------------------------------------------------------------------------
+constexpr int kRowTile = 1024;    // cells of a row segment
+constexpr int kRowThreads = 256;  // threads of the block
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+template <class R> struct BulkArgs {
+    const R *__restrict__ fin;
+    R *__restrict__ fout;
+    int64_t nx, ny, ncell;
+    Shift sh;
+    int kind;
+    int slot;  // elements per plane slot in shared memory (kRowTile + 2 * 16 / sizeof(R))
+    Counters *cnt;
+};
+
+template <class Sys, class R, bool ENTROPIC>
+__global__ void __launch_bounds__(kRowThreads) k_stage_bulk(BulkArgs<R> a, ParamsR<R> P)
+{
+    constexpr int Q = Sys::Q, M = Sys::M, NP = Q * M;
+    constexpr int V4 = 16 / (int)sizeof(R);  // elements per 16 bytes
+    extern __shared__ __align__(128) unsigned char smem_bulk[];
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(smem_bulk);
+    R *sm = reinterpret_cast<R *>(smem_bulk + 128);
+    __shared__ int s_off[NP];  // element offset of the run's first needed value in its slot
+    const int64_t y = blockIdx.y;
+    const int64_t x0 = (int64_t)blockIdx.x * kRowTile;
+    const int T = (int)min((int64_t)kRowTile, a.nx - x0);
+    const uint32_t bar = smem_u32(mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // one bulk copy of n elements into shared memory, announced to the mbarrier first
+        auto copy = [&](R *dst, const R *src, int64_t n) {
+            const uint32_t nb = (uint32_t)(n * (int64_t)sizeof(R));
+            asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(nb) : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(dst)),
+                "l"(src), "r"(nb), "r"(bar)
+                : "memory");
+        };
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int64_t r = a.sh.roff[k];
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                const int p = k * M + m;
+                const R *plane = a.fin + (int64_t)p * a.ncell;
+                R *dst = sm + (int64_t)p * a.slot;
+                if (Lattice<2>::axis(k) == 0) {
+                    int64_t sx = x0 + r;
+                    if (sx >= a.nx) sx -= a.nx;
+                    const int64_t al = sx - (sx % V4);
+                    const int off = (int)(sx - al);
+                    const int64_t L = (off + T + V4 - 1) / V4 * V4;  // whole 16-byte units
+                    const int64_t first = min(L, a.nx - al);
+                    s_off[p] = off;
+                    copy(dst, plane + y * a.nx + al, first);
+                    if (first < L) copy(dst + first, plane + y * a.nx, L - first);  // wrap to the row start
+                } else {
+                    int64_t sy = y + r;
+                    if (sy >= a.ny) sy -= a.ny;
+                    s_off[p] = 0;
+                    copy(dst, plane + sy * a.nx + x0, (T + V4 - 1) / V4 * V4);
+                }
+            }
+        }
+        unsigned long long state;
+        asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(bar) : "memory");
+        (void)state;
+    }
+    __syncthreads();  // s_off visible
+    // bounded wait for phase 0 of the mbarrier
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 22) && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar)
+            : "memory");
+    }
+    if (__syncthreads_or(!done)) {  // the whole block gives up together
+        if (threadIdx.x == 0) atomicAdd(&a.cnt->copy_timeouts, 1ull);
+        return;
+    }
+    for (int j0 = 0; j0 < kRowTile; j0 += kRowThreads) {  // same trip count for every thread
+        const int j = j0 + threadIdx.x;
+        const bool valid = j < T;
+        bool fb = false, inc = false;
+        if (valid) {
+            R f[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) f[p] = sm[(int64_t)p * a.slot + s_off[p] + j];
+            R w;
+            relax_cell<Sys, R, ENTROPIC, false>(P, f, a.kind, fb, inc, w);
+            const int64_t o = y * a.nx + x0 + j;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) a.fout[(int64_t)p * a.ncell + o] = f[p];
+        }
+        if constexpr (ENTROPIC && !Sys::LINEAR) warp_count(fb, &a.cnt->fallbacks);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Temporally blocked 1D composite step.  One block owns an output tile of T
 // cells and loads a window of W = T + 2H cells of every plane into shared
 // memory, H = sum |s_i| over the fused stages.  In shared memory the transport

@@ -597,7 +597,7 @@ __device__ R entropic_omega(const ParamsR<R> &P, const typename Sys::template Ct
     R Flo = -Em, Fhi = R(0);
     bool hi_ok = false;
     R t;
-    bool last = false, last_newton = false;
+    bool last = false, last_newton = false, extra = false;
     R Bp, dBp;
     if (R(1) < hi && Sys::template eval<R, 1>(P, cx, R(1), Bp, dBp, nullptr, bw)) {
         warm2 = true;
@@ -630,21 +630,28 @@ __device__ R entropic_omega(const ParamsR<R> &P, const typename Sys::template Ct
                 // vanishes at t = 1 in F).  When r is at the rounding level of B the model root
                 // is as good as an exact evaluation at it would certify: return it, lowered by
                 // the model's error bound over F'(tm) so that F stays <= 0.
+                // The even content beyond the model, c6 (t^6 - 1) + ..., is not measured; near
+                // t = 1 it is about 6 c6 (t - 1), and c6 is estimated from the decay of the
+                // series, c6 ~ c4^2 / c2, which must be at the rounding level too.
                 const R r = (dBp + dEm) - R(3) * (Bp - Em);
                 const R tol = R(64) * R(1.1920929e-7) * (Bp + Em);
                 const R dm = tm * (R(2) * b2 + tm * (R(3) * b3 + R(4) * b4 * tm));
-                if (fabs(r) <= tol && dm > R(0)) {
-                    const R tc = tm - qdiv(fabs(r) + tol, dm);
+                const R even = R(6) * qdiv(b4 * b4, fabs(b2)) * fabs(tm - R(1));
+                // and only for smooth cells (cubic term small against the quadratic one), where the
+                // rounding-level difference between tm and the root is immaterial; rough cells take
+                // the exact evaluation, whose chord is accurate to second order
+                if (fabs(r) <= tol && even <= tol && dm > R(0) && fabs(b3) <= R(1e-3) * b2) {
+                    const R tc = tm - qdiv(fabs(r) + even, dm);
                     return R(1) + (tc > R(0) ? tc : R(0));
                 }
             }
             t = tm;
             last = sizeof(R) == 4;  // FP32: one exact evaluation at the model root
             last_newton = true;
-        } else if (sizeof(R) == 4) {
-            // FP32, model root on the wrong side of t = 1: F(1) is then at the rounding level
-            // of B (the odd part of B(t) is O(|delta|^3), below FP32 resolution for small
-            // deviations), and iterating on such values would only chase noise.  Take what the
+        } else if (sizeof(R) == 4 && fabs(F1) <= R(64) * R(1.1920929e-7) * (Bp + Em)) {
+            // FP32, model root on the wrong side of t = 1 with F(1) at the rounding level of B
+            // (the odd part of B(t) is O(|delta|^3), below FP32 resolution for small
+            // deviations): iterating on such values would only chase noise.  Take what the
             // two evaluations bracket: F(1) <= 0 allows omega = 2; F(1) > 0 gives the chord
             // through F(0) = -E0 and F(1), which does not exceed the root of a convex F.
             return F1 < R(0) ? R(2) : R(1) + Em / Bp;
@@ -669,7 +676,22 @@ __device__ R entropic_omega(const ParamsR<R> &P, const typename Sys::template Ct
             Fhi = F;
             hi_ok = ok;
         }
-        if (last || (ok && F == R(0))) break;
+        if (ok && F == R(0)) break;
+        if (last) {
+            // FP32, the evaluation at the model root fell below the root with no upper point:
+            // the Newton point from it lies above the root of the convex F, so when it is not
+            // already within the rounding level one more evaluation there closes a bracket for
+            // the chord (rough cells only; smooth ones are certified or bracketed already)
+            if (sizeof(R) == 4 && !extra && !hi_ok && ok && dF > R(0)) {
+                const R tn = t - F / dF;
+                extra = true;
+                if (tn - t > R(1e-6) * t && tn < hi) {
+                    t = tn;
+                    continue;
+                }
+            }
+            break;
+        }
         bool newton = ok && dF > R(0);
         R tn = newton ? t - F / dF : R(-1);
         if (!(tn > lo && tn < hi)) {

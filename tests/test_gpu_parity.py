@@ -40,6 +40,13 @@ CASES = {
                   lambda nx, ny: inputs.burgers_2d(nx, ny, seed=5, noise=1e-3)),
     "linear2d": (2, "linear", 300, 7, dict(V=1.0, a=(0.2, -0.15)), lambda nx, ny: inputs.linear_sine_2d(nx, ny)),
     "sw2d": (2, "sw", 33, 27, dict(V=8.0, g=9.81), lambda nx, ny: inputs.sw_random_2d(nx, ny, seed=6)),
+    # rows whose length is a multiple of 16 bytes take the bulk-copy staged stage kernel: several
+    # row segments with a ragged last one, and a row narrower than the shifts (wrap at both ends)
+    "burgers2d_rows": (2, "burgers", 1032, 6, dict(V=3.0, c=(1.0, 0.6)),
+                       lambda nx, ny: inputs.burgers_2d(nx, ny, seed=8, noise=1e-3)),
+    "sw2d_rows": (2, "sw", 1032, 3, dict(V=8.0, g=9.81),
+                  lambda nx, ny: inputs.sw_random_2d(nx, ny, seed=9, h_amp=0.03, u_amp=0.03)),
+    "linear2d_narrow": (2, "linear", 4, 9, dict(V=1.0, a=(0.2, -0.15)), lambda nx, ny: inputs.linear_sine_2d(nx, ny)),
 }
 EULER = {
     "euler_vortex": (2, "euler", 40, 36, dict(V=8.0, gamma=1.4), lambda nx, ny: inputs.euler_vortex_2d(nx, ny)),
