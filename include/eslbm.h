@@ -191,7 +191,9 @@ eslbm_status eslbm_read_distributions(eslbm_handle *h, double *f_out, int32_t on
 eslbm_status eslbm_read_totals(eslbm_handle *h, double *out, int32_t on_device);
 
 /* Counters accumulated by the stage kernels since the last reset (synchronizes).
-   Returns ESLBM_WARN_OMEGA_FALLBACK when fallbacks > 0. */
+   Returns ESLBM_WARN_OMEGA_FALLBACK when fallbacks > 0, and ESLBM_ERR_CUDA if a
+   2D stage staged by bulk copies gave up waiting for them (its cells were then
+   not relaxed; not expected to happen). */
 eslbm_status eslbm_get_diagnostics(eslbm_handle *h, eslbm_diagnostics *out);
 eslbm_status eslbm_reset_diagnostics(eslbm_handle *h);
 

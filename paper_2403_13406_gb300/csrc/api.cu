@@ -657,6 +657,7 @@ eslbm_status eslbm_get_diagnostics(eslbm_handle *h, eslbm_diagnostics *out)
     const bool seen = c.omega_min_bits != 0x7f800000u;
     out->omega_min = seen ? (double)wmin : NAN;
     out->omega_max = seen ? (double)wmax : NAN;
+    if (c.copy_timeouts) return fail(h, ESLBM_ERR_CUDA, "a staged 2D stage gave up waiting for its bulk copies");
     return c.fallbacks ? ESLBM_WARN_OMEGA_FALLBACK : ESLBM_OK;
 }
 
