@@ -336,7 +336,7 @@ eslbm_status eslbm_gradient(eslbm_handle *h, const double *u0, const double *dJ_
             CK(cudaMemcpyAsync(outer(i / K), h->f[h->cur], sb, cudaMemcpyDeviceToDevice, h->stream), "checkpoint");
             ck_pending[(size_t)(i / K)] = h->pending;
         }
-        if ((s = run_ops(h)) != ESLBM_OK) return s;
+        if ((s = run_unit(h, 1)) != ESLBM_OK) return s;  // the fused kernel where there is one
     }
     // cotangent of the final physical state from the cotangent of the moments
     int g = 0;
@@ -354,7 +354,7 @@ eslbm_status eslbm_gradient(eslbm_handle *h, const double *u0, const double *dJ_
         for (int64_t j = 0; j < s1 - s0; ++j) {
             CK(cudaMemcpyAsync(inner(j), h->f[h->cur], sb, cudaMemcpyDeviceToDevice, h->stream), "step state");
             step_pending[(size_t)j] = h->pending;
-            if ((s = run_ops(h)) != ESLBM_OK) return s;
+            if ((s = run_unit(h, 1)) != ESLBM_OK) return s;
         }
         for (int64_t j = s1 - s0 - 1; j >= 0; --j) {
             // recompute the step stage by stage, keeping every stage's input
