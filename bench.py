@@ -171,7 +171,10 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "sw1d_d1q2_entropic", "N_sample": n_cells, "V": V, "g": G},
+            "data": "synthetic",
+            "config": {"workload": "sw1d_d1q2_entropic_n%d_t%g" % (args.n, args.t_final), "system": "shallow_water",
+                       "lattice": "D1Q2", "N": args.n, "V": V, "g": G, "t_final": args.t_final, "omega": "entropic",
+                       "N_sample": n_cells, "steps_per_sample": 1},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
