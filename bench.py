@@ -496,9 +496,12 @@ def batch_leg(torch, eslbm, inputs, stream, dev, count=64, steps=20, grad_instan
     [256, 1024]^2 with 8-mode Fourier depth data, advanced by one cooperative launch per composite step
     replayed from CUDA graphs, after the autotuner has picked the schedule; a bounded number of steps.
     The reverse mode is timed on the first `grad_instances` instances (L2 misfit of the final depth
-    against a seeded target, checkpoints every grad_K steps)."""
+    against a seeded target, checkpoints every grad_K steps).  FP32 storage shifted by the state at rest
+    of depth 1; its error after the timed steps is stated against FP64 single-lattice runs of two
+    instances."""
     sizes = inputs.batched_sizes(count, 256, 1024)
-    cfg = eslbm.make_config(2, "sw", 1, 1, V=BATCH_V, g=G, precision="fp32", omega_mode="entropic")
+    cfg = eslbm.make_config(2, "sw", 1, 1, V=BATCH_V, g=G, precision="fp32", omega_mode="entropic",
+                            u_ref=(1.0, 0.0, 0.0))
     with torch.cuda.stream(stream):
         b = eslbm.Batch(cfg, sizes, stream=stream, device=dev)
         u0 = b.pack([inputs.sw_fourier_2d(nx, ny, seed=1000 + i) for i, (nx, ny) in enumerate(sizes)])
@@ -519,6 +522,17 @@ def batch_leg(torch, eslbm, inputs, stream, dev, count=64, steps=20, grad_instan
         ms = e0.elapsed_time(e1)
         fallbacks = int(b.diagnostics()["fallbacks"])
         cells = b.total_cells
+        fp32 = b.moments()
+        errs = []
+        for i in (0, 1):  # FP64 reference of two instances, same steps
+            nx, ny = sizes[i]
+            c64 = eslbm.make_config(2, "sw", nx, ny, V=BATCH_V, g=G, precision="fp64", omega_mode="entropic")
+            s64 = eslbm.Simulation(c64, stream=stream, device=dev)
+            s64.init_equilibrium(torch.from_numpy(inputs.sw_fourier_2d(nx, ny, seed=1000 + i)).to(dev))
+            s64.step(steps)
+            ref = s64.moments()
+            s64.close()
+            errs.append(float(torch.linalg.vector_norm(fp32[i][0] - ref[0]) / torch.linalg.vector_norm(ref[0])))
         b.close()
         # reverse mode on a bounded sample of the instances
         gs = sizes[:grad_instances]
@@ -546,6 +560,8 @@ def batch_leg(torch, eslbm, inputs, stream, dev, count=64, steps=20, grad_instan
                         "steps": steps, "ms": ms, "site_updates_per_s": cells * steps / (ms * 1e-3),
                         "schedule": {"segment": sched[0], "blocks_per_sm": sched[1], "order": sched[2]},
                         "tune_s": tune_s, "cuda_graph": True, "fallbacks": fallbacks, "V": BATCH_V,
+                        "storage": "fp32, shifted, u_ref = (1, 0, 0)",
+                        "rel_l2_h_vs_fp64": {"instances": [list(sizes[0]), list(sizes[1])], "values": errs},
                         "adjoint": {"instances": grad_instances, "steps": grad_n, "checkpoint_every": grad_K,
                                     "forward_s": fwd_s, "gradient_s": adj_s, "ratio": adj_s / fwd_s,
                                     "grad_norm": gnorm}}}

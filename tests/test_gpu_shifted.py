@@ -176,3 +176,19 @@ def test_reference_outside_domain_is_rejected():
     with pytest.raises(eslbm.EslbmError) as e:
         eslbm.Simulation(cfg)
     assert e.value.status == eslbm.ERR_DOMAIN
+
+
+@pytest.mark.parametrize("name", ["sw1d", "burgers2d"])
+def test_shifted_gradient_matches_plain(name):
+    """Reverse mode on the shifted storage: the same gradient as on the plain storage (FP64)."""
+    dim, system, nx, ny, kw, init, uref = CASES[name]
+    u0 = torch.as_tensor(init(nx, ny), device="cuda", dtype=torch.float64)
+    lam = torch.as_tensor(np.random.default_rng(4).standard_normal(u0.shape), device="cuda")
+    out = []
+    for shifted in (False, True):
+        cfg = eslbm.make_config(dim, system, nx, ny, precision="fp64", omega_mode="entropic",
+                                u_ref=uref if shifted else None, **kw)
+        sim = eslbm.Simulation(cfg)
+        out.append(sim.gradient(u0, lam, n=3, K=2).cpu().numpy())
+        sim.close()
+    assert rel_max(out[1], out[0]) <= 1e-10
