@@ -1,10 +1,23 @@
 // family_impl.cuh -- launcher bodies shared by the per-family translation units.
 #pragma once
 
+#include <atomic>
+
 #include "kernels.cuh"
 #include "launch.h"
 
 namespace eslbm {
+
+// Launch settings that belong to a device (function attributes, occupancy, SM
+// count) are cached per device: a process may drive several GPUs.
+constexpr int kMaxDevices = 64;
+
+inline int device_slot()
+{
+    int d = 0;
+    cudaGetDevice(&d);
+    return d < 0 ? 0 : d % kMaxDevices;
+}
 
 template <class Sys, int DIM, class R, bool ENT, bool DIAG>
 cudaError_t stage_one(const StageLaunch &L)
@@ -16,11 +29,12 @@ cudaError_t stage_one(const StageLaunch &L)
             constexpr int NP = Sys::Q * Sys::M;
             BulkArgs<R> b{(const R *)L.fin, (R *)L.fout, L.nx, L.ny, L.ncell, L.sh, L.kind, kRowTile + 2 * V4, L.cnt};
             const size_t smem = 128 + (size_t)NP * (size_t)b.slot * sizeof(R);
-            static bool attr = false;
-            if (!attr) {
+            static std::atomic<int> attr[kMaxDevices];
+            const int d = device_slot();
+            if (!attr[d].load()) {
                 cudaFuncSetAttribute(k_stage_bulk<Sys, R, ENT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)(128 + 16 * (kRowTile + 4) * sizeof(double)));
-                attr = true;
+                attr[d].store(1);
             }
             dim3 grid((unsigned)((L.nx + kRowTile - 1) / kRowTile), (unsigned)L.ny);
             k_stage_bulk<Sys, R, ENT><<<grid, kRowThreads, smem, L.stream>>>(b, params_as<R>(L.P));
@@ -53,9 +67,6 @@ cudaError_t stage_family(bool fp64, bool entropic, bool diag, const StageLaunch 
     return fp64 ? stage_prec<Sys, DIM, double>(entropic, diag, L) : stage_prec<Sys, DIM, float>(entropic, diag, L);
 }
 
-// Tile of the fused 1D kernel: about four resident blocks per SM over the grid
-// (a multiple of 32 cells), at least 128 cells, and a window that fits 96 KiB of
-// shared memory.
 // Tile of the temporally blocked 1D kernel: enough tiles to give every SM
 // `bps` resident blocks in a single wave, with the window of a block taking
 // at most its share of the SM's shared memory.
@@ -63,12 +74,15 @@ constexpr int kSmemPerSm = 220 * 1024;
 
 inline int fused_tile(int64_t n, int halo, int bytes_per_cell, int bps)
 {
-    static int sms = 0;
+    static std::atomic<int> sm_count[kMaxDevices];
+    const int d = device_slot();
+    int sms = sm_count[d].load();
     if (!sms) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
+        sm_count[d].store(sms);
     }
     int64_t t = (n + (int64_t)bps * sms - 1) / ((int64_t)bps * sms);
     t = ((t + 31) / 32) * 32;
@@ -82,13 +96,16 @@ template <class Sys, class R, bool ENT>
 cudaError_t fused_one(const FusedLaunch &L)
 {
     constexpr int NP = Sys::Q * Sys::M;
-    static int bps = 0;  // resident blocks per SM allowed by the registers (at most 4)
+    static std::atomic<int> bps_cache[kMaxDevices];  // resident blocks per SM allowed by the registers (<= 4)
+    const int d = device_slot();
+    int bps = bps_cache[d].load();
     if (!bps) {
         cudaFuncSetAttribute(k_step1d<Sys, R, ENT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPerSm);
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step1d<Sys, R, ENT>, kFusedBlock, 0) != cudaSuccess)
             occ = 1;
         bps = occ < 1 ? 1 : (occ > 4 ? 4 : occ);
+        bps_cache[d].store(bps);
     }
     const int tile = fused_tile(L.n, L.sl.halo, NP * (int)sizeof(R), bps);
     if (tile < 32) return cudaErrorInvalidValue;
