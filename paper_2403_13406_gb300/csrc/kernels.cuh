@@ -675,6 +675,27 @@ __global__ void __launch_bounds__(kBlock) k_gather(const R *__restrict__ f, doub
     }
 }
 
+// Sum of v over a block of kRedThreads threads in a fixed order (deterministic,
+// independent of scheduling): a shuffle tree inside each warp, then the warp
+// sums, in warp order, by a shuffle tree in the first warp.  The total is
+// returned to thread 0; part holds kRedThreads / 32 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double *part)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) part[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = lane < kRedThreads / 32 ? part[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    __syncthreads();  // part is reused by the next call
+    return t;
+}
+
 // Totals (double precision): per cell Sigma(f) = S(u) + sum_k B_k(f_k - f^eq_k),
 // S(u), and u.  Pass 1: fixed grid of kRedBlocks blocks, each reducing a fixed
 // set of cells in a fixed tree order into partials[block][2 + M].
@@ -717,19 +738,12 @@ __global__ void __launch_bounds__(kRedThreads) k_totals_partial(const R *__restr
 #pragma unroll
         for (int m = 0; m < M; ++m) acc[2 + m] += u[m];
     }
-    __shared__ double sm[NV][kRedThreads];
+    __shared__ double part[kRedThreads / 32];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sm[v][threadIdx.x] = acc[v];
-    __syncthreads();
-    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-#pragma unroll
-            for (int v = 0; v < NV; ++v) sm[v][threadIdx.x] += sm[v][threadIdx.x + s];
-        __syncthreads();
+    for (int v = 0; v < NV; ++v) {
+        const double t = block_sum(acc[v], part);
+        if (threadIdx.x == 0) partials[(int64_t)blockIdx.x * NV + v] = t;
     }
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int v = 0; v < NV; ++v) partials[(int64_t)blockIdx.x * NV + v] = sm[v][0];
 }
 
 // Pass 2: one block sums the partials in a fixed order.
@@ -738,18 +752,12 @@ __global__ void __launch_bounds__(kRedThreads) k_totals_final(const double *__re
                                                               int nblocks)
 {
     constexpr int nv = NV;
-    __shared__ double sm[kRedThreads];
+    __shared__ double part[kRedThreads / 32];
     for (int v = 0; v < nv; ++v) {
         double a = 0.0;
         for (int b = threadIdx.x; b < nblocks; b += blockDim.x) a += partials[(int64_t)b * nv + v];
-        sm[threadIdx.x] = a;
-        __syncthreads();
-        for (int s = kRedThreads / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[v] = sm[0];
-        __syncthreads();
+        const double t = block_sum(a, part);
+        if (threadIdx.x == 0) out[v] = t;
     }
 }
 
