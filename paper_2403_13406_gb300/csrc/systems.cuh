@@ -570,10 +570,10 @@ struct Euler2 {
 //     omega delta); FP64 iterates to a relative step of 1e-9 and evaluates once
 //     more.  In FP32 the inner solves of the evaluation at +1 and of the later
 //     ones start from the deviations already found at -1 (and +1), which
-//     leaves one inner Newton step to do instead of two; and when the spare
-//     datum of the model certifies it to the rounding level (smooth data), the
-//     model root itself is returned, lowered by the error bound, without the
-//     evaluation at it.
+//     leaves one inner Newton step to do instead of two.  In both precisions,
+//     when the spare datum of the model certifies it to the rounding level of
+//     the arithmetic (smooth data), the model root itself is returned, lowered
+//     by the error estimate, without further evaluations.
 //  4. Return the chord root of the final bracket: for a convex F it never
 //     exceeds t*, so the cell's microscopic entropy does not increase.  If
 //     Newton converged from below (every evaluation <= 0 at rounding level),
@@ -623,8 +623,8 @@ __device__ R entropic_omega(const ParamsR<R> &P, const typename Sys::template Ct
             tm -= qdiv(m, dm);
         }
         if (tm > lo && tm < hi) {
-            if (sizeof(R) == 4 && fabs(tm - R(1)) <= R(0.25)) {
-                // FP32: the four values fix the quartic model with one datum to spare.  Its
+            if (fabs(tm - R(1)) <= R(0.25)) {
+                // The four values fix the quartic model with one datum to spare.  Its
                 // residual r = (B'(1) + B'(-1)) - 3 (B(1) - B(-1)) is 4 c5 + 14 c7 + ... for
                 // B(t) = sum_n c_n t^n, the odd content the model misses (the even content
                 // vanishes at t = 1 in F).  When r is at the rounding level of B the model root
@@ -634,7 +634,8 @@ __device__ R entropic_omega(const ParamsR<R> &P, const typename Sys::template Ct
                 // t = 1 it is about 6 c6 (t - 1), and c6 is estimated from the decay of the
                 // series, c6 ~ c4^2 / c2, which must be at the rounding level too.
                 const R r = (dBp + dEm) - R(3) * (Bp - Em);
-                const R tol = R(64) * R(1.1920929e-7) * (Bp + Em);
+                const R eps = sizeof(R) == 4 ? R(1.1920929e-7) : R(2.220446049250313e-16);
+                const R tol = R(64) * eps * (Bp + Em);
                 const R dm = tm * (R(2) * b2 + tm * (R(3) * b3 + R(4) * b4 * tm));
                 const R even = R(6) * qdiv(b4 * b4, fabs(b2)) * fabs(tm - R(1));
                 // and only for smooth cells (cubic term small against the quadratic one), where the
