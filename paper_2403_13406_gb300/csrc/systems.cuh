@@ -567,8 +567,9 @@ struct Euler2 {
 //     [lo, hi] with F(lo) <= 0 < F(hi) (outside the convexity domain counts as
 //     above the root).  FP32 stops after the first exact evaluation at the
 //     model root (its O(|delta|^3) error is below the storage rounding of
-//     omega delta); FP64 iterates to a relative step of 1e-9 and evaluates once
-//     more.  In FP32 the inner solves of the evaluation at +1 and of the later
+//     omega delta), adding one at the Newton point when that evaluation fell
+//     below the root with no upper point; FP64 iterates to a relative step of
+//     1e-9 and evaluates once more.  In FP32 the inner solves of the evaluation at +1 and of the later
 //     ones start from the deviations already found at -1 (and +1), which
 //     leaves one inner Newton step to do instead of two.  In both precisions,
 //     when the spare datum of the model certifies it to the rounding level of
