@@ -58,3 +58,20 @@ def test_euler_vortex_conserves_and_converges(scheme):
         ex = inputs.euler_vortex_2d(N, N, centre=(5 + n * dt, 5 + n * dt))
         errs.append(math.sqrt(float(np.mean((u[0] - ex[0]) ** 2))))
     assert errs[1] < errs[0] / 4
+
+
+def test_euler_vortex_fourth_order():
+    """The isentropic vortex is an exact solution (translated by t (1, 1)): at t = 0.9375 the oracle's
+    error falls at fourth order between 128^2 and 256^2 cells (measured 4.43; scheme I, omega = 2)."""
+    errs = []
+    for N in (128, 256):
+        m = model(N)
+        u0 = inputs.euler_vortex_2d(N, N)
+        f = O.init_equilibrium(m, u0)
+        dt = 24 * (10.0 / N) / 8.0
+        n = N // 32
+        O.composite_steps(m, f, n, scheme="I")
+        u = O.moments(m, f)
+        ex = inputs.euler_vortex_2d(N, N, centre=(5 + n * dt, 5 + n * dt))
+        errs.append(math.sqrt((10.0 / N) ** 2 * float(np.sum((u[0] - ex[0]) ** 2))))
+    assert math.log2(errs[0] / errs[1]) > 4.0
