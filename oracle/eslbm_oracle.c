@@ -3,7 +3,7 @@
  * header).  Built with -O2 -ffp-contract=off and without fast-math so that
  * every operation is a plain IEEE double operation on both x86 and Arm.
  *
- * Readings of the paper used here (each one is also listed in the design doc):
+ * Readings of the paper used here, where it is silent or ambiguous:
  *  - Negative time steps reverse the shift direction only; the relaxation is
  *    unchanged (Section 2.1, eq. symmetryCondition and the remark after it).
  *  - Kinetic entropies of the nonlinear D2Q4 models are not printed in the
