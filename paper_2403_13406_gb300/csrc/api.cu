@@ -361,16 +361,47 @@ eslbm_status eslbm_gradient(eslbm_handle *h, const double *u0, const double *dJ_
             rec.clear();
             const void *in = inner(j);
             int64_t pend = step_pending[(size_t)j];
-            for (const Op &op : h->ops) {
-                if (!op.relax) {
-                    pend += op.shift;
-                    continue;
+            if (fused_path(h)) {
+                // one temporally blocked launch that also writes every stage's output but the last
+                FusedLaunch L;
+                L.sl.n = 0;
+                L.sl.halo = 0;
+                for (const Op &op : h->ops) {
+                    if (!op.relax) {
+                        pend += op.shift;
+                        continue;
+                    }
+                    if (L.sl.n >= kMaxFusedStages || pend > (1 << 20) || pend < -(1 << 20))
+                        return fail(h, ESLBM_ERR_ARG, "step cannot be fused");
+                    rec.push_back({L.sl.n == 0 ? in : stage(L.sl.n - 1), pend, op.kind});
+                    L.sl.shift[L.sl.n] = (int)pend;
+                    L.sl.kind[L.sl.n] = op.kind;
+                    L.sl.halo += (int)(pend < 0 ? -pend : pend);
+                    L.sl.n += 1;
+                    pend = 0;
                 }
-                void *out = stage((int64_t)rec.size());
-                if ((s = stage_between(h, in, out, pend, op.kind)) != ESLBM_OK) return s;
-                rec.push_back({in, pend, op.kind});
-                in = out;
-                pend = 0;
+                L.fin = in;
+                L.fout = stage(L.sl.n - 1);
+                L.n = h->cfg.nx;
+                L.cnt = h->counters();
+                L.P = h->P;
+                L.stream = h->stream;
+                L.rec = stage(0);
+                L.rec_stride_bytes = (int64_t)G.stride;
+                L.nrec = L.sl.n - 1;
+                CK(launch_fused1d(h->family, h->fp64, entropic, L), "recording step launch");
+            } else {
+                for (const Op &op : h->ops) {
+                    if (!op.relax) {
+                        pend += op.shift;
+                        continue;
+                    }
+                    void *out = stage((int64_t)rec.size());
+                    if ((s = stage_between(h, in, out, pend, op.kind)) != ESLBM_OK) return s;
+                    rec.push_back({in, pend, op.kind});
+                    in = out;
+                    pend = 0;
+                }
             }
             // reverse sweep of the stages: reverse shift and transposed relaxation Jacobian
             for (int64_t st = (int64_t)rec.size() - 1; st >= 0; --st) {

@@ -92,17 +92,18 @@ inline int fused_tile(int64_t n, int halo, int bytes_per_cell, int bps)
     return (int)t;
 }
 
-template <class Sys, class R, bool ENT>
-cudaError_t fused_one(const FusedLaunch &L)
+template <class Sys, class R, bool ENT, bool REC>
+cudaError_t fused_one_rec(const FusedLaunch &L)
 {
     constexpr int NP = Sys::Q * Sys::M;
     static std::atomic<int> bps_cache[kMaxDevices];  // resident blocks per SM allowed by the registers (<= 4)
     const int d = device_slot();
     int bps = bps_cache[d].load();
     if (!bps) {
-        cudaFuncSetAttribute(k_step1d<Sys, R, ENT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPerSm);
+        cudaFuncSetAttribute(k_step1d<Sys, R, ENT, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPerSm);
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step1d<Sys, R, ENT>, kFusedBlock, 0) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step1d<Sys, R, ENT, REC>, kFusedBlock, 0) !=
+            cudaSuccess)
             occ = 1;
         bps = occ < 1 ? 1 : (occ > 4 ? 4 : occ);
         bps_cache[d].store(bps);
@@ -110,10 +111,17 @@ cudaError_t fused_one(const FusedLaunch &L)
     const int tile = fused_tile(L.n, L.sl.halo, NP * (int)sizeof(R), bps);
     if (tile < 32) return cudaErrorInvalidValue;
     const size_t smem = (size_t)(tile + 2 * L.sl.halo) * NP * sizeof(R);
-    FusedArgs<R> a{(const R *)L.fin, (R *)L.fout, L.n, tile, L.cnt};
+    FusedArgs<R> a{(const R *)L.fin, (R *)L.fout, L.n, tile, L.cnt,
+                   (R *)L.rec, L.rec_stride_bytes / (int64_t)sizeof(R), L.nrec};
     const unsigned grid = (unsigned)((L.n + tile - 1) / tile);
-    k_step1d<Sys, R, ENT><<<grid, kFusedBlock, smem, L.stream>>>(a, L.sl, params_as<R>(L.P));
+    k_step1d<Sys, R, ENT, REC><<<grid, kFusedBlock, smem, L.stream>>>(a, L.sl, params_as<R>(L.P));
     return cudaGetLastError();
+}
+
+template <class Sys, class R, bool ENT>
+cudaError_t fused_one(const FusedLaunch &L)
+{
+    return L.rec ? fused_one_rec<Sys, R, ENT, true>(L) : fused_one_rec<Sys, R, ENT, false>(L);
 }
 
 template <class Sys>

@@ -306,9 +306,14 @@ template <class R> struct FusedArgs {
     int64_t n;       // cells
     int tile;        // T
     Counters *cnt;
+    // recording (reverse mode): the output of stage i < nrec is also written, in the physical
+    // layout, to rec + i * rec_stride
+    R *rec;
+    int64_t rec_stride;
+    int nrec;
 };
 
-template <class Sys, class R, bool ENTROPIC>
+template <class Sys, class R, bool ENTROPIC, bool RECORD = false>
 __global__ void __launch_bounds__(kFusedBlock, sizeof(R) == 4 ? 4 : 2)
     k_step1d(FusedArgs<R> a, StageList sl, ParamsR<R> P)
 {
@@ -363,6 +368,21 @@ __global__ void __launch_bounds__(kFusedBlock, sizeof(R) == 4 ? 4 : 2)
             if constexpr (ENTROPIC && !Sys::LINEAR) warp_count(fb, &a.cnt->fallbacks);
         }
         __syncthreads();
+        if constexpr (RECORD) {
+            if (st < a.nrec) {  // the tile is exact after every stage
+                R *dst = a.rec + (int64_t)st * a.rec_stride;
+                for (int j = threadIdx.x; j < T; j += blockDim.x) {
+#pragma unroll
+                    for (int k = 0; k < Q; ++k) {
+                        int i = j + H - off[k];
+                        i = i < 0 ? i + W : (i >= W ? i - W : i);
+#pragma unroll
+                        for (int m = 0; m < M; ++m) dst[(int64_t)(k * M + m) * a.n + x0 + j] = sm[(k * M + m) * W + i];
+                    }
+                }
+                __syncthreads();  // the next stage rewrites the window in place
+            }
+        }
     }
     // write the exact tile
     for (int j = threadIdx.x; j < T; j += blockDim.x) {

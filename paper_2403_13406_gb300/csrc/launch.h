@@ -30,6 +30,9 @@ struct FusedLaunch {
     Counters *cnt;
     Params P;
     cudaStream_t stream;
+    void *rec = nullptr;         // optional: the outputs of the first nrec stages go to rec + i * rec_stride
+    int64_t rec_stride_bytes = 0;
+    int nrec = 0;
 };
 
 // temporally blocked 1D step (several stages in shared memory); 1D families only
