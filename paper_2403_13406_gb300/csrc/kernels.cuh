@@ -441,12 +441,13 @@ __device__ __forceinline__ void relax_adjoint(const ParamsR<R> &P, const R *f, c
     R w = P.omega;
     bool varying = false;
     typename Sys::template Ctx<R> cx;
+    R Dm[Q * M];  // dual deviations at t = -1, from the root-find's own evaluation there
     if constexpr (ENTROPIC && !Sys::LINEAR) {
         Sys::template prepare<R>(P, u, delta, cx);
         bool fb = false;
-        w = entropic_omega<Sys, R>(P, cx, fb);
-        R E0, d0;
-        varying = !fb && Sys::template eval<R>(P, cx, R(-1), E0, d0) && E0 > R(0);
+        R E0 = R(0);
+        w = entropic_omega<Sys, R>(P, cx, fb, Dm, &E0);
+        varying = !fb && E0 > R(0);
     } else if constexpr (ENTROPIC) {
         w = R(2);
     }
@@ -457,8 +458,8 @@ __device__ __forceinline__ void relax_adjoint(const ParamsR<R> &P, const R *f, c
     if constexpr (ENTROPIC && !Sys::LINEAR) {
         if (varying) {
             const R t = w - R(1);
-            R Dt[Q * M], Dm[Q * M], B, dB, Bm, dBm;
-            const bool ok = Sys::template eval<R>(P, cx, t, B, dB, Dt) & Sys::template eval<R>(P, cx, R(-1), Bm, dBm, Dm);
+            R Dt[Q * M], B, dB;
+            const bool ok = Sys::template eval<R>(P, cx, t, B, dB, Dt);
             R dg = R(0);
 #pragma unroll
             for (int i = 0; i < Q * M; ++i) dg += delta[i] * gout[i];

@@ -583,13 +583,17 @@ struct Euler2 {
 // ---------------------------------------------------------------------------
 
 template <class Sys, class R>
-__device__ R entropic_omega(const ParamsR<R> &P, const typename Sys::template Ctx<R> &cx, bool &fallback)
+__device__ R entropic_omega(const ParamsR<R> &P, const typename Sys::template Ctx<R> &cx, bool &fallback,
+                           R *Dm = nullptr, R *E0 = nullptr)
 {
+    // (Dm, E0: optional outputs of the evaluation at t = -1, the dual deviations and B(-1))
     fallback = false;
-    R Em, dEm;
+    R Em = R(0), dEm;
     R bw[2 * Sys::Q];  // deviations at t = -1 and t = +1: warm starts of the later evaluations
     bool warm2 = false;
-    if (!Sys::template eval<R, 0>(P, cx, R(-1), Em, dEm, nullptr, bw)) {
+    const bool okm = Sys::template eval<R, 0>(P, cx, R(-1), Em, dEm, Dm, bw);
+    if (E0) *E0 = okm ? Em : R(0);
+    if (!okm) {
         fallback = true;
         return R(1);
     }
