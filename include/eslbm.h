@@ -230,7 +230,9 @@ eslbm_status eslbm_gradient_workspace(const eslbm_config *cfg, int64_t n, int64_
    of the configured scheme from f_0 = f^eq(u0).  u0, dJ_duT, dJ_du0: M double
    planes in device memory.  The forward pass keeps the state every K steps in ws;
    the reverse pass recomputes each K-step segment (keeping every step's starting
-   state), then each step stage by stage (keeping every stage's input), and applies
+   state), then each step stage by stage (keeping every stage's input; in 1D one
+   launch of the temporally blocked kernel that also writes every stage's output),
+   and applies
    the adjoint stages in reverse: the reverse shift of the transport and the
    transposed Jacobian of the relaxation, including the derivative of the entropic
    omega by the implicit function theorem on eq. variableOmegaProblem.  On return
