@@ -62,6 +62,7 @@ def parse():
                    help="run one secondary measurement alone and print its JSON (for profiling)")
     p.add_argument("--hbm-steps", type=int, default=20, help="composite steps of the 2D streaming leg")
     p.add_argument("--hbm-case", default=None, help="one case of the 2D streaming leg (default: all)")
+    p.add_argument("--batch-count", type=int, default=64, help="instances of the batched leg")
     return p.parse_args()
 
 
@@ -197,7 +198,7 @@ def main():
         stream = torch.cuda.Stream(device=dev)
         leg = {"hbm2d": hbm2d_leg, "batched": batch_leg, "fp32err": fp32err_leg}[args.leg]
         kw = ({"steps": args.hbm_steps, "only": args.hbm_case} if args.leg == "hbm2d" else
-              {"N": args.n, "t_final": args.t_final} if args.leg == "fp32err" else {})
+              {"N": args.n, "t_final": args.t_final} if args.leg == "fp32err" else {"count": args.batch_count})
         print(json.dumps(leg(torch, eslbm, inputs, stream, dev, **kw)), flush=True)
         return
 
