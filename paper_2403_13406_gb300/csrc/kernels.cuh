@@ -335,13 +335,20 @@ __global__ void __launch_bounds__(kFusedBlock, sizeof(R) == 4 ? 4 : 2)
     int off[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) off[k] = 0;
+    int moved = 0;  // sum of |shift| over the stages so far
     for (int st = 0; st < sl.n; ++st) {
         const int s = sl.shift[st], kind = sl.kind[st];
 #pragma unroll
         for (int k = 0; k < Q; ++k) off[k] += Lattice<1>::sign(k) * s;
-        const int jend = ((W + 31) / 32) * 32;  // whole warps for the warp-level counters
-        for (int j = threadIdx.x; j < jend; j += blockDim.x) {
-            const bool valid = j < W;
+        moved += s < 0 ? -s : s;
+        // only window cells within the later stages' total shift (H - moved) of the tile can still
+        // reach it: [moved, W - moved).  Their pulls read [moved - |s|, W - moved + |s|), the range
+        // the previous stage computed.
+        const int jlo = moved, cnt = W - 2 * moved;
+        const int jend = ((cnt + 31) / 32) * 32;  // whole warps for the warp-level counters
+        for (int jj = threadIdx.x; jj < jend; jj += blockDim.x) {
+            const int j = jlo + jj;
+            const bool valid = jj < cnt;
             bool fb = false, inc = false;
             if (valid) {
                 int slot[Q];
