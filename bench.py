@@ -40,13 +40,13 @@ BATCH_V = 8.0  # lattice velocity of the batched 2D shallow-water instances: sqr
 L2_FLUSH_BYTES = 512 << 20
 # FP32 roofline of the dominant kernel (the fused composite step k_step1d, entropic shallow water):
 # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz; and the FP32 operations of one cell-stage
-# (FADD + FMUL + 2 FFMA counted by ncu on this workload: 8.20e9 flops per launch over 607 blocks x
-# 1800 window cells x 18 stages).  The kernel is bound by instruction issue: 634 thread instructions
+# (FADD + FMUL + 2 FFMA counted by ncu on this workload: 7.98e9 flops per launch over the 19.25e6
+# cell-stages a launch computes, 607 blocks x 31716).  The kernel is bound by instruction issue: 641 thread instructions
 # per cell-stage against 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FLOPS_PER_CELL_STAGE = 417.0
+FLOPS_PER_CELL_STAGE = 415.0
 ISSUE_PEAK_TINST = 152 * 4 * 32 * 2.07e9 / 1e12
-INST_PER_CELL_STAGE = 634.0
+INST_PER_CELL_STAGE = 641.0
 
 
 def parse():
