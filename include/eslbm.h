@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define ESLBM_ABI_VERSION 2
+#define ESLBM_ABI_VERSION 3
 
 typedef enum {
     ESLBM_OK = 0,
@@ -61,7 +61,20 @@ typedef enum {
    SHALLOW_WATER: (h, hu[, hv]) with gravity g (Example 3).  EULER: (rho, rho u,
    rho v, E) with gamma-law pressure (Section 6.3), fixed omega only. */
 enum { ESLBM_LINEAR = 0, ESLBM_BURGERS = 1, ESLBM_SHALLOW_WATER = 2, ESLBM_EULER = 3 };
-enum { ESLBM_FP32 = 0, ESLBM_FP64 = 1 };
+/* Precision.  FP32 / FP64: storage and all arithmetic of the relaxation in that
+   type (the reported reductions are FP64 in every mode).  FP32_MIXED (no
+   counterpart in the paper): FP32 storage and FP32 root-find iterations, with the
+   entropy difference of the entropic omega evaluated in FP64 -- E0 = B(-1) and
+   the residual F(t) = B(t) - E0 at the returned root, B(t) = sum_k B_k(t delta_k)
+   (Section 4, eq. variableOmegaProblem); when F(t) > 0 the chord root through
+   (0, -E0) and (t, F(t)), which never exceeds the root of the convex F, replaces
+   t.  With a fixed omega FP32_MIXED is FP32. */
+enum { ESLBM_FP32 = 0, ESLBM_FP64 = 1, ESLBM_FP32_MIXED = 2 };
+/* Temporal blocking: AUTO runs several fused stages per launch from on-chip
+   memory where a kernel for it exists (1D: every step); OFF runs one launch per
+   fused stage (the same per-cell arithmetic; used to cross-check the blocked
+   kernels). */
+enum { ESLBM_BLOCKING_AUTO = 0, ESLBM_BLOCKING_OFF = 1 };
 enum { ESLBM_OMEGA_FIXED = 0, ESLBM_OMEGA_ENTROPIC = 1 };
 /* Schemes (I)-(IV) of Section 6.1; PLAIN is the standard scheme R T(kappa dx/V)
    of Section 2.1 (one stage per step); B is scheme (B) of Section 6.3,
@@ -75,7 +88,7 @@ enum { ESLBM_RELAX_MAIN = 0, ESLBM_RELAX_PROJECT = 1 };
 typedef struct {
     int32_t dim;        /* 1 (D1Q2) or 2 (D2Q4) */
     int32_t system;     /* ESLBM_LINEAR, ESLBM_BURGERS, ESLBM_SHALLOW_WATER, ESLBM_EULER */
-    int32_t precision;  /* ESLBM_FP32 or ESLBM_FP64: storage and arithmetic of the distributions */
+    int32_t precision;  /* ESLBM_FP32, ESLBM_FP64 or ESLBM_FP32_MIXED (see above) */
     int32_t omega_mode; /* ESLBM_OMEGA_FIXED or ESLBM_OMEGA_ENTROPIC */
     int32_t scheme;     /* ESLBM_SCHEME_* */
     int32_t kappa;      /* shift unit V dt / (24 dx) >= 1 (Section 2.3; the paper uses 1) */
@@ -87,9 +100,12 @@ typedef struct {
     double g;           /* gravity (shallow water) */
     double gamma;       /* ratio of specific heats (Euler) */
     double t_max;       /* entropic mode: omega - 1 is searched in [0, t_max]; 0 -> 3 */
-    int32_t diagnostics;/* 1: count per-cell entropy increases and track omega min/max */
+    int32_t diagnostics;/* 1: check every entropic relaxation per cell and track omega min/max
+                           (eslbm_diagnostics); the same kernels run, the results do not change */
     int32_t shifted;    /* 1: store g = f - fbar with fbar_k = f^eq_k(u_ref) (see below); 0: store f */
     double u_ref[4];    /* reference conserved state of the shifted storage (M values used) */
+    int32_t blocking;   /* ESLBM_BLOCKING_AUTO or ESLBM_BLOCKING_OFF */
+    int32_t reserved;   /* 0 */
 } eslbm_config;
 
 /* Shifted storage (no counterpart in the paper).  With shifted = 1 the state
@@ -116,11 +132,19 @@ typedef struct {
     int64_t step_cells;      /* lattice time of one step in units of dx / V (24 kappa for I-IV) */
 } eslbm_sizes;
 
+/* Per-cell entropy check (diagnostics = 1, entropic omega, Section 4): for every
+   relaxation the kernel evaluates, in FP64 from the moments and deviations it
+   used and with its own constants, F(omega - 1) = B(omega - 1) - B(-1), the change
+   of the cell's microscopic entropy under R_omega.  entropy_increases counts the
+   cells where F exceeds 64 unit roundoffs of B(-1) in the arithmetic that chose
+   omega (FP32, or FP64 for FP64 and FP32_MIXED); entropy_excess_max is the largest
+   F / B(-1) seen (0 if never positive). */
 typedef struct {
     uint64_t relaxations;        /* cell relaxations since the last reset */
     uint64_t fallbacks;          /* cells that used omega = 1 (no entropic root) */
-    uint64_t entropy_increases;  /* cells whose Sigma increased (diagnostics = 1) */
+    uint64_t entropy_increases;  /* cells whose Sigma increased (diagnostics = 1, see above) */
     double omega_min, omega_max; /* range of omega used (diagnostics = 1) */
+    double entropy_excess_max;   /* largest F(omega - 1) / B(-1) (diagnostics = 1, see above) */
 } eslbm_diagnostics;
 
 typedef struct eslbm_handle eslbm_handle;
@@ -211,12 +235,19 @@ eslbm_status eslbm_reset_diagnostics(eslbm_handle *h);
    call then synchronizes the stream).  Same fixed-order reduction as
    eslbm_read_totals.
    The first call on a device looks up the scratch's device address on the current
-   device; make that first call before any stream capture.  All calls share the
-   scratch (it keeps the last call's contents; every call overwrites what it reads),
-   so calls that overlap on the GPU, e.g. on two streams, race.
-   Errors: ESLBM_ERR_ARG for a bad cfg, a null or misaligned pointer, or totals that
-   do not fit the scratch (more than 8, i.e. M > 6); ESLBM_ERR_CUDA on a failed
-   CUDA call. */
+   device; make that first call before any stream capture.  The address is then
+   cached for the life of the process: after cudaDeviceReset, or any other teardown
+   of the device's primary context, it is stale, and the call must not be used again
+   in that process.  All calls share the scratch (it keeps the last call's contents;
+   every call overwrites what it reads), so calls that overlap on the GPU, e.g. on
+   two streams, race.
+   A call made while `stream` is being captured into a CUDA graph must pass
+   out_on_device = 1: the host copy of out_on_device = 0 ends with a stream
+   synchronization, which capture forbids, so such a call returns ESLBM_ERR_ARG and
+   records nothing.
+   Errors: ESLBM_ERR_ARG for a bad cfg, a null or misaligned pointer, totals that
+   do not fit the scratch (more than 8, i.e. M > 6), or out_on_device = 0 on a
+   capturing stream; ESLBM_ERR_CUDA on a failed CUDA call. */
 eslbm_status eslbm_read_totals_noalloc(const eslbm_config *cfg, const void *f, int64_t pending_shift,
                                        double *out, int32_t out_on_device, void *stream);
 
@@ -331,8 +362,10 @@ eslbm_status eslbm_batch_gradient_workspace(const eslbm_config *base, int32_t co
 eslbm_status eslbm_batch_gradient(eslbm_batch *b, const double *u0, const double *dJ_duT, double *dJ_du0, int64_t n,
                                   int64_t K, void *ws, uint64_t ws_bytes);
 
-/* Fallback count of the batched kernels since creation (synchronizes; the omega
-   range is not tracked, returned as 0).  ESLBM_WARN_OMEGA_FALLBACK when > 0. */
+/* Counters of the batched kernels since creation (synchronizes): fallbacks, and
+   with base.diagnostics = 1 the per-cell entropy check and the omega range as in
+   eslbm_get_diagnostics (relaxations is not tracked, returned as 0).
+   ESLBM_WARN_OMEGA_FALLBACK when fallbacks > 0. */
 eslbm_status eslbm_batch_get_diagnostics(eslbm_batch *b, eslbm_diagnostics *out);
 
 #ifdef __cplusplus

@@ -30,7 +30,9 @@ eslbm_status validate(const eslbm_config *c)
     if (!c) return ESLBM_ERR_ARG;
     if (c->dim != 1 && c->dim != 2) return ESLBM_ERR_ARG;
     if (c->system < ESLBM_LINEAR || c->system > ESLBM_EULER) return ESLBM_ERR_ARG;
-    if (c->precision != ESLBM_FP32 && c->precision != ESLBM_FP64) return ESLBM_ERR_ARG;
+    if (c->precision != ESLBM_FP32 && c->precision != ESLBM_FP64 && c->precision != ESLBM_FP32_MIXED)
+        return ESLBM_ERR_ARG;
+    if (c->blocking != ESLBM_BLOCKING_AUTO && c->blocking != ESLBM_BLOCKING_OFF) return ESLBM_ERR_ARG;
     if (c->omega_mode != ESLBM_OMEGA_FIXED && c->omega_mode != ESLBM_OMEGA_ENTROPIC) return ESLBM_ERR_ARG;
     if (c->scheme < ESLBM_SCHEME_I || c->scheme > ESLBM_SCHEME_B) return ESLBM_ERR_ARG;
     if (c->kappa < 1 || c->kappa > 1024) return ESLBM_ERR_ARG;
@@ -62,6 +64,7 @@ struct eslbm_handle {
     eslbm_sizes sz;
     int family;
     bool fp64;
+    int om;  // OmegaMode
     void *f[2];
     int cur;
     char *ws;
@@ -138,8 +141,7 @@ eslbm_status launch_one_stage(eslbm_handle *h, int64_t shift, int kind)
     L.cnt = h->counters();
     L.P = h->P;
     L.stream = h->stream;
-    const bool entropic = h->cfg.omega_mode == ESLBM_OMEGA_ENTROPIC;
-    CK(launch_stage(h->family, h->fp64, entropic, h->cfg.diagnostics != 0, L), "stage launch");
+    CK(launch_stage(h->family, h->fp64, h->om, h->cfg.diagnostics != 0, L), "stage launch");
     h->cur = 1 - h->cur;
     h->relaxations += (uint64_t)h->sz.ncell;
     return ESLBM_OK;
@@ -159,9 +161,9 @@ eslbm_status run_ops(eslbm_handle *h)
     return ESLBM_OK;
 }
 
-// 1D runs without per-cell diagnostics use the temporally blocked kernel: the
-// stages of `steps` consecutive steps (merged shifts, as in run_ops) in one launch.
-bool fused_path(const eslbm_handle *h) { return h->cfg.dim == 1 && h->cfg.diagnostics == 0; }
+// 1D runs use the temporally blocked kernel (unless blocking is off): the stages of
+// `steps` consecutive steps (merged shifts, as in run_ops) in one launch.
+bool fused_path(const eslbm_handle *h) { return h->cfg.dim == 1 && h->cfg.blocking == ESLBM_BLOCKING_AUTO; }
 
 // steps fused into one launch: one composite step, or up to 24 steps of the short schemes
 int64_t fused_group(const eslbm_handle *h)
@@ -198,7 +200,7 @@ eslbm_status run_fused(eslbm_handle *h, int64_t steps)
     L.cnt = h->counters();
     L.P = h->P;
     L.stream = h->stream;
-    CK(launch_fused1d(h->family, h->fp64, h->cfg.omega_mode == ESLBM_OMEGA_ENTROPIC, L), "fused step launch");
+    CK(launch_fused1d(h->family, h->fp64, h->om, h->cfg.diagnostics != 0, L), "fused step launch");
     h->cur = 1 - h->cur;
     h->relaxations += (uint64_t)h->sz.ncell * (uint64_t)L.sl.n;
     return ESLBM_OK;
@@ -293,7 +295,7 @@ eslbm_status stage_between(eslbm_handle *h, const void *fin, void *fout, int64_t
     L.cnt = h->counters();
     L.P = h->P;
     L.stream = h->stream;
-    CK(launch_stage(h->family, h->fp64, h->cfg.omega_mode == ESLBM_OMEGA_ENTROPIC, false, L), "stage launch");
+    CK(launch_stage(h->family, h->fp64, h->om, false, L), "stage launch");
     return ESLBM_OK;
 }
 
@@ -345,7 +347,6 @@ eslbm_status eslbm_gradient(eslbm_handle *h, const double *u0, const double *dJ_
        "adjoint readout");
     std::vector<int64_t> step_pending((size_t)G.inner, 0);
     std::vector<RecordedStage> rec;
-    const bool entropic = h->cfg.omega_mode == ESLBM_OMEGA_ENTROPIC;
     for (int64_t c = G.n_outer - 1; c >= 0 && n > 0; --c) {
         const int64_t s0 = c * K, s1 = std::min(n, s0 + K);
         // recompute the segment, keeping every step's starting state
@@ -389,7 +390,7 @@ eslbm_status eslbm_gradient(eslbm_handle *h, const double *u0, const double *dJ_
                 L.rec = stage(0);
                 L.rec_stride_bytes = (int64_t)G.stride;
                 L.nrec = L.sl.n - 1;
-                CK(launch_fused1d(h->family, h->fp64, entropic, L), "recording step launch");
+                CK(launch_fused1d(h->family, h->fp64, h->om, false, L), "recording step launch");
             } else {
                 for (const Op &op : h->ops) {
                     if (!op.relax) {
@@ -415,7 +416,7 @@ eslbm_status eslbm_gradient(eslbm_handle *h, const double *u0, const double *dJ_
                 A.kind = rec[(size_t)st].kind;
                 A.P = h->P;
                 A.stream = h->stream;
-                CK(launch_adjoint_stage(h->family, h->fp64, entropic, A), "adjoint stage");
+                CK(launch_adjoint_stage(h->family, h->fp64, h->om, A), "adjoint stage");
                 g = 1 - g;
             }
         }
@@ -480,6 +481,7 @@ eslbm_status eslbm_create(const eslbm_config *cfg, void *f_a, void *f_b, void *w
     h->sz = sz;
     h->family = family_of(*cfg);
     h->fp64 = cfg->precision == ESLBM_FP64;
+    h->om = omega_mode_of(*cfg);
     h->f[0] = f_a;
     h->f[1] = f_b;
     h->cur = 0;
@@ -688,6 +690,9 @@ eslbm_status eslbm_get_diagnostics(eslbm_handle *h, eslbm_diagnostics *out)
     const bool seen = c.omega_min_bits != 0x7f800000u;
     out->omega_min = seen ? (double)wmin : NAN;
     out->omega_max = seen ? (double)wmax : NAN;
+    float ex;
+    std::memcpy(&ex, &c.excess_max_bits, sizeof(float));
+    out->entropy_excess_max = (double)ex;
     if (c.copy_timeouts) return fail(h, ESLBM_ERR_CUDA, "a staged 2D stage gave up waiting for its bulk copies");
     return c.fallbacks ? ESLBM_WARN_OMEGA_FALLBACK : ESLBM_OK;
 }

@@ -72,7 +72,8 @@ struct eslbm_batch {
     int32_t count;
     Layout L;
     int family;
-    bool fp64, entropic;
+    bool fp64;
+    int om;  // OmegaMode
     void *pool[2];
     int side;
     char *ws;
@@ -189,7 +190,7 @@ eslbm_status run_step(eslbm_batch *b)
     B.P = b->P;
     B.grid = std::max(1, std::min(b->n_items, b->sms * b->blocks_per_sm));
     B.stream = b->stream;
-    BCK(launch_batch_step(b->family, b->fp64, b->entropic, B), "batch step launch");
+    BCK(launch_batch_step(b->family, b->fp64, b->om, b->cfg.diagnostics != 0, B), "batch step launch");
     if (B.sl.n & 1) b->side ^= 1;
     return ESLBM_OK;
 }
@@ -269,7 +270,7 @@ eslbm_status eslbm_batch_create(const eslbm_config *base, int32_t count, const i
     b->L = L;
     b->family = family_of(*base);
     b->fp64 = base->precision == ESLBM_FP64;
-    b->entropic = base->omega_mode == ESLBM_OMEGA_ENTROPIC;
+    b->om = omega_mode_of(*base);
     b->pool[0] = pool_a;
     b->pool[1] = pool_b;
     b->side = 0;
@@ -285,7 +286,7 @@ eslbm_status eslbm_batch_create(const eslbm_config *base, int32_t count, const i
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-    b->max_bps = batch_blocks_per_sm(b->family, b->fp64, b->entropic);
+    b->max_bps = batch_blocks_per_sm(b->family, b->fp64, b->om, b->cfg.diagnostics != 0);
     if (b->sms < 1 || b->max_bps < 1) {
         delete b;
         return ESLBM_ERR_CUDA;
@@ -552,7 +553,15 @@ eslbm_status eslbm_batch_get_diagnostics(eslbm_batch *b, eslbm_diagnostics *out)
     BCK(cudaStreamSynchronize(b->stream), "sync");
     std::memset(out, 0, sizeof(*out));
     out->fallbacks = c.fallbacks;
-    out->omega_min = out->omega_max = 0.0;
+    out->entropy_increases = c.entropy_increases;
+    float wmin, wmax, ex;
+    std::memcpy(&wmin, &c.omega_min_bits, sizeof(float));
+    std::memcpy(&wmax, &c.omega_max_bits, sizeof(float));
+    std::memcpy(&ex, &c.excess_max_bits, sizeof(float));
+    const bool seen = c.omega_min_bits != 0x7f800000u;
+    out->omega_min = seen ? (double)wmin : NAN;
+    out->omega_max = seen ? (double)wmax : NAN;
+    out->entropy_excess_max = (double)ex;
     return c.fallbacks ? ESLBM_WARN_OMEGA_FALLBACK : ESLBM_OK;
 }
 

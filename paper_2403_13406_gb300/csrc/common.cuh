@@ -69,6 +69,11 @@ template <class R> inline ParamsR<R> params_as(const Params &P)
 
 enum { KIND_MAIN = 0, KIND_PROJECT = 1 };
 
+// How a kernel chooses omega: the fixed value, the entropic root in the storage
+// precision, or (FP32 storage only) the entropic root with the entropy
+// difference evaluated in FP64.
+enum OmegaMode { OM_FIXED = 0, OM_ENTROPIC = 1, OM_MIXED = 2 };
+
 // Velocity sets of Section 1.2: D1Q2 = (+V, -V); D2Q4 = (+V,0), (0,+V), (-V,0), (0,-V).
 template <int DIM> struct Lattice;
 template <> struct Lattice<1> {
@@ -88,7 +93,10 @@ struct Shift {
     int64_t roff[4];
 };
 
-// Stages fused into one launch of the temporally blocked 1D kernel.
+// Stages fused into one launch of a temporally blocked kernel.  halo must equal
+// the sum of |shift| over the stages: the kernels size their windows by it and
+// compute, at each stage, only the cells that can still reach the output tile
+// (the launchers reject a list whose halo differs).
 constexpr int kMaxFusedStages = 64;
 struct StageList {
     int n;                       // stages
@@ -96,6 +104,14 @@ struct StageList {
     int shift[kMaxFusedStages];  // transport before each relaxation
     int kind[kMaxFusedStages];   // KIND_MAIN or KIND_PROJECT
 };
+
+inline bool stage_list_ok(const StageList &sl)
+{
+    if (sl.n < 1 || sl.n > kMaxFusedStages) return false;
+    long long h = 0;
+    for (int i = 0; i < sl.n; ++i) h += sl.shift[i] < 0 ? -(long long)sl.shift[i] : sl.shift[i];
+    return h == sl.halo;
+}
 
 // Batched execution: independent instances of one system on grids of their own
 // size, packed in one pool per ping-pong side, cut into work items.
@@ -118,7 +134,9 @@ struct Counters {
     unsigned long long domain_violations;
     unsigned long long non_finite;
     unsigned long long copy_timeouts;  // bulk-copy waits that gave up (never expected; reported as an error)
-    unsigned long long pad[2];
+    unsigned int excess_max_bits;      // float bits of the largest per-cell F(omega - 1) / B(-1) seen (>= 0)
+    unsigned int pad0;
+    unsigned long long pad1;
 };
 
 template <class R> struct Tol;

@@ -6,36 +6,42 @@
 
 namespace eslbm {
 
-cudaError_t stage_scalar(int, bool, bool, bool, const StageLaunch &);
-cudaError_t stage_sw(int, bool, bool, bool, const StageLaunch &);
+cudaError_t stage_scalar(int, bool, int, bool, const StageLaunch &);
+cudaError_t stage_sw1(bool, int, bool, const StageLaunch &);
+cudaError_t stage_sw2(bool, int, bool, const StageLaunch &);
 cudaError_t init_scalar(int, bool, const double *, void *, int64_t, const Params &, Counters *, cudaStream_t);
-cudaError_t init_sw(int, bool, const double *, void *, int64_t, const Params &, Counters *, cudaStream_t);
+cudaError_t init_sw1(bool, const double *, void *, int64_t, const Params &, Counters *, cudaStream_t);
+cudaError_t init_sw2(bool, const double *, void *, int64_t, const Params &, Counters *, cudaStream_t);
 cudaError_t totals_scalar(int, bool, const void *, double *, double *, int64_t, int64_t, const Shift &,
                           const Params &, cudaStream_t);
-cudaError_t totals_sw(int, bool, const void *, double *, double *, int64_t, int64_t, const Shift &, const Params &,
-                      cudaStream_t);
+cudaError_t totals_sw1(bool, const void *, double *, double *, int64_t, int64_t, const Shift &, const Params &,
+                       cudaStream_t);
+cudaError_t totals_sw2(bool, const void *, double *, double *, int64_t, int64_t, const Shift &, const Params &,
+                       cudaStream_t);
 
-cudaError_t fused_scalar(int, bool, bool, const FusedLaunch &);
-cudaError_t fused_sw(int, bool, bool, const FusedLaunch &);
+cudaError_t fused_scalar(int, bool, int, bool, const FusedLaunch &);
+cudaError_t fused_sw1(bool, int, bool, const FusedLaunch &);
 
-cudaError_t launch_fused1d(int family, bool fp64, bool entropic, const FusedLaunch &L)
+cudaError_t launch_fused1d(int family, bool fp64, int om, bool diag, const FusedLaunch &L)
 {
-    if (family == FAM_SW1) return fused_sw(family, fp64, entropic, L);
-    if (family == FAM_LINEAR1 || family == FAM_BURGERS1) return fused_scalar(family, fp64, entropic, L);
+    if (family == FAM_SW1) return fused_sw1(fp64, om, diag, L);
+    if (family == FAM_LINEAR1 || family == FAM_BURGERS1) return fused_scalar(family, fp64, om, diag, L);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_stage(int family, bool fp64, bool entropic, bool diag, const StageLaunch &L)
+cudaError_t launch_stage(int family, bool fp64, int om, bool diag, const StageLaunch &L)
 {
-    if (family == FAM_SW1 || family == FAM_SW2) return stage_sw(family, fp64, entropic, diag, L);
-    if (family == FAM_EULER2) return stage_family<Euler2, 2>(fp64, false, false, L);
-    return stage_scalar(family, fp64, entropic, diag, L);
+    if (family == FAM_SW1) return stage_sw1(fp64, om, diag, L);
+    if (family == FAM_SW2) return stage_sw2(fp64, om, diag, L);
+    if (family == FAM_EULER2) return stage_family<Euler2, 2>(fp64, OM_FIXED, false, L);
+    return stage_scalar(family, fp64, om, diag, L);
 }
 
 cudaError_t launch_init_eq(int family, bool fp64, const double *u0, void *f, int64_t ncell, const Params &P,
                            Counters *cnt, cudaStream_t st)
 {
-    if (family == FAM_SW1 || family == FAM_SW2) return init_sw(family, fp64, u0, f, ncell, P, cnt, st);
+    if (family == FAM_SW1) return init_sw1(fp64, u0, f, ncell, P, cnt, st);
+    if (family == FAM_SW2) return init_sw2(fp64, u0, f, ncell, P, cnt, st);
     if (family == FAM_EULER2) return init_family<Euler2>(fp64, u0, f, ncell, P, cnt, st);
     return init_scalar(family, fp64, u0, f, ncell, P, cnt, st);
 }
@@ -43,7 +49,8 @@ cudaError_t launch_init_eq(int family, bool fp64, const double *u0, void *f, int
 cudaError_t launch_totals(int family, bool fp64, const void *f, double *partials, double *out, int64_t nx,
                           int64_t ny, const Shift &sh, const Params &P, cudaStream_t st)
 {
-    if (family == FAM_SW1 || family == FAM_SW2) return totals_sw(family, fp64, f, partials, out, nx, ny, sh, P, st);
+    if (family == FAM_SW1) return totals_sw1(fp64, f, partials, out, nx, ny, sh, P, st);
+    if (family == FAM_SW2) return totals_sw2(fp64, f, partials, out, nx, ny, sh, P, st);
     if (family == FAM_EULER2) return totals_family<Euler2, 2>(fp64, f, partials, out, nx, ny, sh, P, st);
     return totals_scalar(family, fp64, f, partials, out, nx, ny, sh, P, st);
 }
@@ -165,23 +172,27 @@ bool reference_state(int family, bool fp64, const double *u_ref, Params &P)
     return false;
 }
 
-cudaError_t adjoint_scalar(int, bool, bool, const AdjointLaunch &);
-cudaError_t adjoint_sw(int, bool, bool, const AdjointLaunch &);
+cudaError_t adjoint_scalar(int, bool, int, const AdjointLaunch &);
+cudaError_t adjoint_sw1(bool, int, const AdjointLaunch &);
+cudaError_t adjoint_sw2(bool, int, const AdjointLaunch &);
 cudaError_t adjoint_init_scalar(int, bool, const double *, const void *, double *, int64_t, const Params &,
                                 cudaStream_t);
-cudaError_t adjoint_init_sw(int, bool, const double *, const void *, double *, int64_t, const Params &, cudaStream_t);
+cudaError_t adjoint_init_sw1(bool, const double *, const void *, double *, int64_t, const Params &, cudaStream_t);
+cudaError_t adjoint_init_sw2(bool, const double *, const void *, double *, int64_t, const Params &, cudaStream_t);
 
-cudaError_t launch_adjoint_stage(int family, bool fp64, bool entropic, const AdjointLaunch &L)
+cudaError_t launch_adjoint_stage(int family, bool fp64, int om, const AdjointLaunch &L)
 {
-    if (family == FAM_SW1 || family == FAM_SW2) return adjoint_sw(family, fp64, entropic, L);
-    if (family == FAM_EULER2) return adjoint_family<Euler2, 2>(fp64, false, L);
-    return adjoint_scalar(family, fp64, entropic, L);
+    if (family == FAM_SW1) return adjoint_sw1(fp64, om, L);
+    if (family == FAM_SW2) return adjoint_sw2(fp64, om, L);
+    if (family == FAM_EULER2) return adjoint_family<Euler2, 2>(fp64, OM_FIXED, L);
+    return adjoint_scalar(family, fp64, om, L);
 }
 
 cudaError_t launch_adjoint_init(int family, bool fp64, const double *u0, const void *g, double *du0, int64_t ncell,
                                 const Params &P, cudaStream_t st)
 {
-    if (family == FAM_SW1 || family == FAM_SW2) return adjoint_init_sw(family, fp64, u0, g, du0, ncell, P, st);
+    if (family == FAM_SW1) return adjoint_init_sw1(fp64, u0, g, du0, ncell, P, st);
+    if (family == FAM_SW2) return adjoint_init_sw2(fp64, u0, g, du0, ncell, P, st);
     if (family == FAM_EULER2) return adjoint_init_family<Euler2>(fp64, u0, g, du0, ncell, P, st);
     return adjoint_init_scalar(family, fp64, u0, g, du0, ncell, P, st);
 }
@@ -200,24 +211,24 @@ cudaError_t launch_adjoint_readout(int dim, bool fp64, const double *lam, void *
     return cudaGetLastError();
 }
 
-cudaError_t batch_scalar(int, bool, bool, const BatchLaunch &);
-cudaError_t batch_sw(int, bool, bool, const BatchLaunch &);
-int batch_occ_scalar(int, bool, bool);
-int batch_occ_sw(int, bool, bool);
+cudaError_t batch_scalar(int, bool, int, bool, const BatchLaunch &);
+cudaError_t batch_sw2(bool, int, bool, const BatchLaunch &);
+int batch_occ_scalar(int, bool, int, bool);
+int batch_occ_sw2(bool, int, bool);
 
-cudaError_t launch_batch_step(int family, bool fp64, bool entropic, const BatchLaunch &L)
+cudaError_t launch_batch_step(int family, bool fp64, int om, bool diag, const BatchLaunch &L)
 {
-    if (family == FAM_SW2) return batch_sw(family, fp64, entropic, L);
-    if (family == FAM_EULER2) return batch_family<Euler2>(fp64, false, L);
-    if (family == FAM_LINEAR2 || family == FAM_BURGERS2) return batch_scalar(family, fp64, entropic, L);
+    if (family == FAM_SW2) return batch_sw2(fp64, om, diag, L);
+    if (family == FAM_EULER2) return batch_family<Euler2>(fp64, OM_FIXED, false, L);
+    if (family == FAM_LINEAR2 || family == FAM_BURGERS2) return batch_scalar(family, fp64, om, diag, L);
     return cudaErrorInvalidValue;
 }
 
-int batch_blocks_per_sm(int family, bool fp64, bool entropic)
+int batch_blocks_per_sm(int family, bool fp64, int om, bool diag)
 {
-    if (family == FAM_SW2) return batch_occ_sw(family, fp64, entropic);
-    if (family == FAM_EULER2) return batch_occ_family<Euler2>(fp64, false);
-    if (family == FAM_LINEAR2 || family == FAM_BURGERS2) return batch_occ_scalar(family, fp64, entropic);
+    if (family == FAM_SW2) return batch_occ_sw2(fp64, om, diag);
+    if (family == FAM_EULER2) return batch_occ_family<Euler2>(fp64, OM_FIXED, false);
+    if (family == FAM_LINEAR2 || family == FAM_BURGERS2) return batch_occ_scalar(family, fp64, om, diag);
     return 0;
 }
 

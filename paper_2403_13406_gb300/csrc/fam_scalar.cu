@@ -3,31 +3,31 @@
 
 namespace eslbm {
 
-cudaError_t stage_scalar(int family, bool fp64, bool entropic, bool diag, const StageLaunch &L)
+cudaError_t stage_scalar(int family, bool fp64, int om, bool diag, const StageLaunch &L)
 {
     switch (family) {
-    case FAM_LINEAR1: return stage_family<Scalar<1, false>, 1>(fp64, entropic, diag, L);
-    case FAM_LINEAR2: return stage_family<Scalar<2, false>, 2>(fp64, entropic, diag, L);
-    case FAM_BURGERS1: return stage_family<Scalar<1, true>, 1>(fp64, entropic, diag, L);
-    case FAM_BURGERS2: return stage_family<Scalar<2, true>, 2>(fp64, entropic, diag, L);
+    case FAM_LINEAR1: return stage_family<Scalar<1, false>, 1>(fp64, om, diag, L);
+    case FAM_LINEAR2: return stage_family<Scalar<2, false>, 2>(fp64, om, diag, L);
+    case FAM_BURGERS1: return stage_family<Scalar<1, true>, 1>(fp64, om, diag, L);
+    case FAM_BURGERS2: return stage_family<Scalar<2, true>, 2>(fp64, om, diag, L);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t fused_scalar(int family, bool fp64, bool entropic, const FusedLaunch &L)
+cudaError_t fused_scalar(int family, bool fp64, int om, bool diag, const FusedLaunch &L)
 {
-    if (family == FAM_LINEAR1) return fused_family<Scalar<1, false>>(fp64, entropic, L);
-    if (family == FAM_BURGERS1) return fused_family<Scalar<1, true>>(fp64, entropic, L);
+    if (family == FAM_LINEAR1) return fused_family<Scalar<1, false>>(fp64, om, diag, L);
+    if (family == FAM_BURGERS1) return fused_family<Scalar<1, true>>(fp64, om, diag, L);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t adjoint_scalar(int family, bool fp64, bool entropic, const AdjointLaunch &L)
+cudaError_t adjoint_scalar(int family, bool fp64, int om, const AdjointLaunch &L)
 {
     switch (family) {
-    case FAM_LINEAR1: return adjoint_family<Scalar<1, false>, 1>(fp64, entropic, L);
-    case FAM_LINEAR2: return adjoint_family<Scalar<2, false>, 2>(fp64, entropic, L);
-    case FAM_BURGERS1: return adjoint_family<Scalar<1, true>, 1>(fp64, entropic, L);
-    case FAM_BURGERS2: return adjoint_family<Scalar<2, true>, 2>(fp64, entropic, L);
+    case FAM_LINEAR1: return adjoint_family<Scalar<1, false>, 1>(fp64, om, L);
+    case FAM_LINEAR2: return adjoint_family<Scalar<2, false>, 2>(fp64, om, L);
+    case FAM_BURGERS1: return adjoint_family<Scalar<1, true>, 1>(fp64, om, L);
+    case FAM_BURGERS2: return adjoint_family<Scalar<2, true>, 2>(fp64, om, L);
     }
     return cudaErrorInvalidValue;
 }
@@ -44,17 +44,17 @@ cudaError_t adjoint_init_scalar(int family, bool fp64, const double *u0, const v
     return cudaErrorInvalidValue;
 }
 
-cudaError_t batch_scalar(int family, bool fp64, bool entropic, const BatchLaunch &L)
+cudaError_t batch_scalar(int family, bool fp64, int om, bool diag, const BatchLaunch &L)
 {
-    if (family == FAM_LINEAR2) return batch_family<Scalar<2, false>>(fp64, entropic, L);
-    if (family == FAM_BURGERS2) return batch_family<Scalar<2, true>>(fp64, entropic, L);
+    if (family == FAM_LINEAR2) return batch_family<Scalar<2, false>>(fp64, om, diag, L);
+    if (family == FAM_BURGERS2) return batch_family<Scalar<2, true>>(fp64, om, diag, L);
     return cudaErrorInvalidValue;
 }
 
-int batch_occ_scalar(int family, bool fp64, bool entropic)
+int batch_occ_scalar(int family, bool fp64, int om, bool diag)
 {
-    if (family == FAM_LINEAR2) return batch_occ_family<Scalar<2, false>>(fp64, entropic);
-    if (family == FAM_BURGERS2) return batch_occ_family<Scalar<2, true>>(fp64, entropic);
+    if (family == FAM_LINEAR2) return batch_occ_family<Scalar<2, false>>(fp64, om, diag);
+    if (family == FAM_BURGERS2) return batch_occ_family<Scalar<2, true>>(fp64, om, diag);
     return 0;
 }
 

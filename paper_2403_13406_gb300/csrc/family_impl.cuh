@@ -19,11 +19,11 @@ inline int device_slot()
     return d < 0 ? 0 : d % kMaxDevices;
 }
 
-template <class Sys, int DIM, class R, bool ENT, bool DIAG>
+template <class Sys, int DIM, class R, int OM, bool DIAG>
 cudaError_t stage_one(const StageLaunch &L)
 {
     constexpr int V4 = 16 / (int)sizeof(R);
-    if constexpr (DIM == 2 && !DIAG) {
+    if constexpr (DIM == 2) {
         // rows start on 16-byte boundaries: stage the pulled rows with bulk copies
         if (L.nx % V4 == 0 && ((uintptr_t)L.fin & 15u) == 0) {
             constexpr int NP = Sys::Q * Sys::M;
@@ -32,39 +32,50 @@ cudaError_t stage_one(const StageLaunch &L)
             static std::atomic<int> attr[kMaxDevices];
             const int d = device_slot();
             if (!attr[d].load()) {
-                cudaFuncSetAttribute(k_stage_bulk<Sys, R, ENT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                cudaFuncSetAttribute(k_stage_bulk<Sys, R, OM, DIAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)(128 + 16 * (kRowTile + 4) * sizeof(double)));
                 attr[d].store(1);
             }
             dim3 grid((unsigned)((L.nx + kRowTile - 1) / kRowTile), (unsigned)L.ny);
-            k_stage_bulk<Sys, R, ENT><<<grid, kRowThreads, smem, L.stream>>>(b, params_as<R>(L.P));
+            k_stage_bulk<Sys, R, OM, DIAG><<<grid, kRowThreads, smem, L.stream>>>(b, params_as<R>(L.P));
             return cudaGetLastError();
         }
     }
     StageArgs<R> a{(const R *)L.fin, (R *)L.fout, L.nx, L.ny, L.ncell, L.sh, L.kind, L.cnt};
     dim3 grid((unsigned)((L.nx + kBlock - 1) / kBlock), (unsigned)L.ny);
-    k_stage<Sys, DIM, R, ENT, DIAG><<<grid, kBlock, 0, L.stream>>>(a, params_as<R>(L.P));
+    k_stage<Sys, DIM, R, OM, DIAG><<<grid, kBlock, 0, L.stream>>>(a, params_as<R>(L.P));
     return cudaGetLastError();
 }
 
-template <class Sys, int DIM, class R>
-cudaError_t stage_prec(bool entropic, bool diag, const StageLaunch &L)
+// Calls f.template operator()<OM, DIAG>() for the kernel variant a (system,
+// precision, omega mode, diagnostics) combination uses: fixed omega, and the
+// linear and Euler systems, have a single variant (nothing to root-find or
+// check); the mixed mode exists for FP32 storage only (FP64 storage already
+// evaluates in FP64).
+template <class Sys, class R, class F> cudaError_t with_variant(int om, bool diag, F &&f)
 {
     if constexpr (Sys::LINEAR || Sys::M == 4) {
-        (void)entropic;
+        (void)om;
         (void)diag;
-        return stage_one<Sys, DIM, R, false, false>(L);
+        return f.template operator()<OM_FIXED, false>();
     } else {
-        if (!entropic) return stage_one<Sys, DIM, R, false, false>(L);
-        if (diag) return stage_one<Sys, DIM, R, true, true>(L);
-        return stage_one<Sys, DIM, R, true, false>(L);
+        if (om == OM_FIXED) return f.template operator()<OM_FIXED, false>();
+        if (om == OM_MIXED && sizeof(R) == 4)
+            return diag ? f.template operator()<OM_MIXED, true>() : f.template operator()<OM_MIXED, false>();
+        return diag ? f.template operator()<OM_ENTROPIC, true>() : f.template operator()<OM_ENTROPIC, false>();
     }
 }
 
-template <class Sys, int DIM>
-cudaError_t stage_family(bool fp64, bool entropic, bool diag, const StageLaunch &L)
+template <class Sys, int DIM, class R>
+cudaError_t stage_prec(int om, bool diag, const StageLaunch &L)
 {
-    return fp64 ? stage_prec<Sys, DIM, double>(entropic, diag, L) : stage_prec<Sys, DIM, float>(entropic, diag, L);
+    return with_variant<Sys, R>(om, diag, [&]<int OM, bool DG>() { return stage_one<Sys, DIM, R, OM, DG>(L); });
+}
+
+template <class Sys, int DIM>
+cudaError_t stage_family(bool fp64, int om, bool diag, const StageLaunch &L)
+{
+    return fp64 ? stage_prec<Sys, DIM, double>(om, diag, L) : stage_prec<Sys, DIM, float>(om, diag, L);
 }
 
 // Tile of the temporally blocked 1D kernel: enough tiles to give every SM
@@ -92,17 +103,19 @@ inline int fused_tile(int64_t n, int halo, int bytes_per_cell, int bps)
     return (int)t;
 }
 
-template <class Sys, class R, bool ENT, bool REC>
+template <class Sys, class R, int OM, bool REC, bool DIAG>
 cudaError_t fused_one_rec(const FusedLaunch &L)
 {
     constexpr int NP = Sys::Q * Sys::M;
+    if (!stage_list_ok(L.sl)) return cudaErrorInvalidValue;
     static std::atomic<int> bps_cache[kMaxDevices];  // resident blocks per SM allowed by the registers (<= 4)
     const int d = device_slot();
     int bps = bps_cache[d].load();
     if (!bps) {
-        cudaFuncSetAttribute(k_step1d<Sys, R, ENT, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemPerSm);
+        cudaFuncSetAttribute(k_step1d<Sys, R, OM, REC, DIAG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemPerSm);
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step1d<Sys, R, ENT, REC>, kFusedBlock, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step1d<Sys, R, OM, REC, DIAG>, kFusedBlock, 0) !=
             cudaSuccess)
             occ = 1;
         bps = occ < 1 ? 1 : (occ > 4 ? 4 : occ);
@@ -114,50 +127,41 @@ cudaError_t fused_one_rec(const FusedLaunch &L)
     FusedArgs<R> a{(const R *)L.fin, (R *)L.fout, L.n, tile, L.cnt,
                    (R *)L.rec, L.rec_stride_bytes / (int64_t)sizeof(R), L.nrec};
     const unsigned grid = (unsigned)((L.n + tile - 1) / tile);
-    k_step1d<Sys, R, ENT, REC><<<grid, kFusedBlock, smem, L.stream>>>(a, L.sl, params_as<R>(L.P));
+    k_step1d<Sys, R, OM, REC, DIAG><<<grid, kFusedBlock, smem, L.stream>>>(a, L.sl, params_as<R>(L.P));
     return cudaGetLastError();
 }
 
-template <class Sys, class R, bool ENT>
-cudaError_t fused_one(const FusedLaunch &L)
+template <class Sys, class R>
+cudaError_t fused_prec(int om, bool diag, const FusedLaunch &L)
 {
-    return L.rec ? fused_one_rec<Sys, R, ENT, true>(L) : fused_one_rec<Sys, R, ENT, false>(L);
+    // the recording launch of the reverse mode runs without diagnostics
+    if (L.rec)
+        return with_variant<Sys, R>(om, false, [&]<int OM, bool DG>() { return fused_one_rec<Sys, R, OM, true, false>(L); });
+    return with_variant<Sys, R>(om, diag, [&]<int OM, bool DG>() { return fused_one_rec<Sys, R, OM, false, DG>(L); });
 }
 
 template <class Sys>
-cudaError_t fused_family(bool fp64, bool entropic, const FusedLaunch &L)
+cudaError_t fused_family(bool fp64, int om, bool diag, const FusedLaunch &L)
 {
-    if constexpr (Sys::LINEAR) {
-        (void)entropic;
-        return fp64 ? fused_one<Sys, double, false>(L) : fused_one<Sys, float, false>(L);
-    } else {
-        if (fp64) return entropic ? fused_one<Sys, double, true>(L) : fused_one<Sys, double, false>(L);
-        return entropic ? fused_one<Sys, float, true>(L) : fused_one<Sys, float, false>(L);
-    }
+    return fp64 ? fused_prec<Sys, double>(om, diag, L) : fused_prec<Sys, float>(om, diag, L);
 }
 
 template <class Sys, int DIM, class R>
-cudaError_t adjoint_prec(bool entropic, const AdjointLaunch &L)
+cudaError_t adjoint_prec(int om, const AdjointLaunch &L)
 {
     dim3 grid((unsigned)((L.nx + kBlock - 1) / kBlock), (unsigned)L.ny);
     const ParamsR<R> P = params_as<R>(L.P);
-    if constexpr (!Sys::LINEAR && Sys::M != 4) {
-        if (entropic) {
-            k_adjoint_stage<Sys, DIM, R, true><<<grid, kBlock, 0, L.stream>>>((const R *)L.fin, (const R *)L.gout,
-                                                                             (R *)L.gin, L.nx, L.ny, L.sh, L.kind, P);
-            return cudaGetLastError();
-        }
-    }
-    (void)entropic;
-    k_adjoint_stage<Sys, DIM, R, false><<<grid, kBlock, 0, L.stream>>>((const R *)L.fin, (const R *)L.gout,
-                                                                      (R *)L.gin, L.nx, L.ny, L.sh, L.kind, P);
-    return cudaGetLastError();
+    return with_variant<Sys, R>(om, false, [&]<int OM, bool DG>() {
+        k_adjoint_stage<Sys, DIM, R, OM><<<grid, kBlock, 0, L.stream>>>((const R *)L.fin, (const R *)L.gout,
+                                                                        (R *)L.gin, L.nx, L.ny, L.sh, L.kind, P);
+        return cudaGetLastError();
+    });
 }
 
 template <class Sys, int DIM>
-cudaError_t adjoint_family(bool fp64, bool entropic, const AdjointLaunch &L)
+cudaError_t adjoint_family(bool fp64, int om, const AdjointLaunch &L)
 {
-    return fp64 ? adjoint_prec<Sys, DIM, double>(entropic, L) : adjoint_prec<Sys, DIM, float>(entropic, L);
+    return fp64 ? adjoint_prec<Sys, DIM, double>(om, L) : adjoint_prec<Sys, DIM, float>(om, L);
 }
 
 template <class Sys>
@@ -170,48 +174,43 @@ cudaError_t adjoint_init_family(bool fp64, const double *u0, const void *g, doub
     return cudaGetLastError();
 }
 
-template <class Sys, class R, bool ENT>
+template <class Sys, class R, int OM, bool DIAG>
 cudaError_t batch_one(const BatchLaunch &L)
 {
     BatchArgs<R> a{{(R *)L.pool[0], (R *)L.pool[1]}, L.inst, L.items, L.n_items, L.side, L.cnt};
     StageList sl = L.sl;
     ParamsR<R> P = params_as<R>(L.P);
     void *args[] = {&a, &sl, &P};
-    return cudaLaunchCooperativeKernel((const void *)k_batch_step<Sys, R, ENT>, dim3((unsigned)L.grid), dim3(kBlock),
-                                       args, 0, L.stream);
+    return cudaLaunchCooperativeKernel((const void *)k_batch_step<Sys, R, OM, DIAG>, dim3((unsigned)L.grid),
+                                       dim3(kBlock), args, 0, L.stream);
 }
 
-template <class Sys, class R, bool ENT>
-int batch_occupancy()
+template <class Sys, class R>
+cudaError_t batch_prec(int om, bool diag, const BatchLaunch &L)
+{
+    return with_variant<Sys, R>(om, diag, [&]<int OM, bool DG>() { return batch_one<Sys, R, OM, DG>(L); });
+}
+
+template <class Sys>
+cudaError_t batch_family(bool fp64, int om, bool diag, const BatchLaunch &L)
+{
+    return fp64 ? batch_prec<Sys, double>(om, diag, L) : batch_prec<Sys, float>(om, diag, L);
+}
+
+template <class Sys, class R>
+int batch_occ_prec(int om, bool diag)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<Sys, R, ENT>, kBlock, 0) != cudaSuccess)
-        return 0;
-    return n;
+    cudaError_t e = with_variant<Sys, R>(om, diag, [&]<int OM, bool DG>() {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step<Sys, R, OM, DG>, kBlock, 0);
+    });
+    return e == cudaSuccess ? n : 0;
 }
 
 template <class Sys>
-cudaError_t batch_family(bool fp64, bool entropic, const BatchLaunch &L)
+int batch_occ_family(bool fp64, int om, bool diag)
 {
-    if constexpr (Sys::LINEAR || Sys::M == 4) {
-        (void)entropic;
-        return fp64 ? batch_one<Sys, double, false>(L) : batch_one<Sys, float, false>(L);
-    } else {
-        if (fp64) return entropic ? batch_one<Sys, double, true>(L) : batch_one<Sys, double, false>(L);
-        return entropic ? batch_one<Sys, float, true>(L) : batch_one<Sys, float, false>(L);
-    }
-}
-
-template <class Sys>
-int batch_occ_family(bool fp64, bool entropic)
-{
-    if constexpr (Sys::LINEAR || Sys::M == 4) {
-        (void)entropic;
-        return fp64 ? batch_occupancy<Sys, double, false>() : batch_occupancy<Sys, float, false>();
-    } else {
-        if (fp64) return entropic ? batch_occupancy<Sys, double, true>() : batch_occupancy<Sys, double, false>();
-        return entropic ? batch_occupancy<Sys, float, true>() : batch_occupancy<Sys, float, false>();
-    }
+    return fp64 ? batch_occ_prec<Sys, double>(om, diag) : batch_occ_prec<Sys, float>(om, diag);
 }
 
 template <class Sys>

@@ -97,6 +97,13 @@ inline int family_of(const eslbm_config &c)
     }
 }
 
+// Omega mode of a configuration (launch.h)
+inline int omega_mode_of(const eslbm_config &c)
+{
+    if (c.omega_mode != ESLBM_OMEGA_ENTROPIC) return OM_FIXED;
+    return c.precision == ESLBM_FP32_MIXED ? OM_MIXED : OM_ENTROPIC;
+}
+
 inline int64_t num_M(const eslbm_config &c)
 {
     if (c.system == ESLBM_SHALLOW_WATER) return c.dim + 1;

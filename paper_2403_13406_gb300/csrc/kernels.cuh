@@ -81,16 +81,158 @@ __device__ __forceinline__ void moments_target(const ParamsR<R> &P, const R *f, 
     for (int i = 0; i < Q * M; ++i) tgt[i] += P.rdev[i];
 }
 
+// The kernel's constants in double precision, exactly as the kernel rounded them
+// (a float kernel's g, 1 / (2V), ... promoted), for the diagnostics' FP64 check.
+template <class R> __device__ __forceinline__ ParamsR<double> promote(const ParamsR<R> &p)
+{
+    ParamsR<double> q;
+    q.V = p.V;
+    q.inv2V = p.inv2V;
+    q.a[0] = p.a[0];
+    q.a[1] = p.a[1];
+    q.c[0] = p.c[0];
+    q.c[1] = p.c[1];
+    q.g = p.g;
+    q.gamma_m1 = p.gamma_m1;
+    q.omega = p.omega;
+    q.t_max = p.t_max;
+    q.gV4 = p.gV4;
+    q.inv16gV = p.inv16gV;
+    q.shifted = p.shifted;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        q.ubar[i] = p.ubar[i];
+        q.cm[i] = p.cm[i];
+        q.aux[i] = p.aux[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        q.rdev[i] = p.rdev[i];
+        q.fbar[i] = p.fbar[i];
+    }
+    return q;
+}
+
+// Per-cell check of Section 4 (diagnostics): the change of the cell's microscopic
+// entropy under R_omega, F(omega - 1) = B(omega - 1) - B(-1) with
+// B(t) = sum_k B_k(t delta_k), evaluated in double precision from the moments and
+// deviations the relaxation used and the kernel's own constants.  Returns
+// F / B(-1): -1 for the projection omega = 1, 0 at equilibrium, +inf if a
+// non-trivial omega lies outside the convexity domain.
+template <class Sys, class R>
+__device__ float entropy_excess(const ParamsR<R> &P, const R *u, const R *delta, R w)
+{
+    constexpr int Q = Sys::Q, M = Sys::M;
+    if (w == R(1)) return -1.0f;
+    const ParamsR<double> Pd = promote(P);
+    double ud[M], dd[Q * M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) ud[m] = double(u[m]);
+#pragma unroll
+    for (int i = 0; i < Q * M; ++i) dd[i] = double(delta[i]);
+    typename Sys::template Ctx<double> cx;
+    Sys::template prepare<double>(Pd, ud, dd, cx);
+    double B0, d0, B1, d1;
+    if (!Sys::template eval<double>(Pd, cx, -1.0, B0, d0)) return INFINITY;
+    if (!(B0 > 0.0)) return 0.0f;
+    if (!Sys::template eval<double>(Pd, cx, double(w) - 1.0, B1, d1)) return INFINITY;
+    const double r = (B1 - B0) / B0;
+    return r == r ? float(r) : INFINITY;
+}
+
+// A per-cell entropy increase: F(omega - 1) above the rounding level of the
+// arithmetic that chose omega (FP32, or FP64 for the FP64 storage and the mixed
+// mode), 64 unit roundoffs of B(-1).
+template <class R, int OM> __device__ __forceinline__ bool entropy_increase(float excess)
+{
+    return excess > (sizeof(R) == 4 && OM != OM_MIXED ? 64.0f * 1.1920929e-7f : 64.0f * 2.220446e-16f);
+}
+
+// Entropic omega with the entropy difference in FP64 (FP32 storage).  The FP32
+// root-find's t = omega - 1 is certified by evaluating, in double precision from
+// the same moments and deviations (and the kernel's own constants),
+// E0 = B(-1) = sum_k B_k(-delta_k) and the residual F(t) = B(t) - E0 at the
+// returned root.  F(t) <= 0 keeps omega.  F(t) > 0 (the FP32 root fell above the
+// root by its rounding) replaces t by the chord root through (0, -E0) and
+// (t, F(t)), t E0 / B(t): on a convex F that chord lies above F, so its root never
+// exceeds the root and the cell's microscopic entropy does not increase to FP64
+// rounding (Section 4).  The result is rounded towards zero to FP32 (t, then
+// omega = 1 + t), which keeps that side.  A cell that FP64 finds outside the
+// convexity domain falls back to omega = 1 (counted).
+template <class Sys, class R>
+__device__ R mixed_omega(const ParamsR<R> &P, const R *u, const R *delta, R w, bool &fallback)
+{
+    constexpr int Q = Sys::Q, M = Sys::M;
+    if constexpr (sizeof(R) == 8) {
+        return w;
+    } else {
+        if (fallback || w == R(1)) return w;
+        const ParamsR<double> Pd = promote(P);
+        double ud[M], dd[Q * M];
+#pragma unroll
+        for (int m = 0; m < M; ++m) ud[m] = double(u[m]);
+#pragma unroll
+        for (int i = 0; i < Q * M; ++i) dd[i] = double(delta[i]);
+        typename Sys::template Ctx<double> cx;
+        Sys::template prepare<double>(Pd, ud, dd, cx);
+        double E0, dE0, Bt, dBt;
+        if (!Sys::template eval<double>(Pd, cx, -1.0, E0, dE0)) {
+            fallback = true;
+            return R(1);
+        }
+        if (!(E0 > 0.0)) return w;  // at equilibrium: every omega leaves the cell unchanged
+        const double t = double(w) - 1.0;
+        if (!Sys::template eval<double>(Pd, cx, t, Bt, dBt)) {
+            fallback = true;
+            return R(1);
+        }
+        if (Bt - E0 <= 0.0) return w;
+        const float tc = __double2float_rz(t * E0 / Bt);
+        return __fadd_rz(1.0f, tc);
+    }
+}
+
+// Diagnostics accumulated by a thread over its cells, merged per warp into the
+// device counters at the end of a kernel (every lane of the warp must call flush).
+struct DiagAcc {
+    float wmin, wmax, excess;
+    __device__ DiagAcc() : wmin(INFINITY), wmax(0.0f), excess(0.0f) {}
+    __device__ void add(float w, float ex)
+    {
+        wmin = fminf(wmin, w);
+        wmax = fmaxf(wmax, w);
+        excess = fmaxf(excess, ex);
+    }
+    __device__ void flush(Counters *c) const
+    {
+        float a = wmin, b = wmax, e = excess;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fminf(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
+            e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&c->omega_min_bits, __float_as_uint(a));
+            atomicMax(&c->omega_max_bits, __float_as_uint(b));
+            if (e > 0.0f) atomicMax(&c->excess_max_bits, __float_as_uint(e));
+        }
+    }
+};
+
 // One relaxation of one cell (eq. relaxationDiscretizationOmega), in place.
-template <class Sys, class R, bool ENTROPIC, bool DIAG>
+// With DIAG the cell's entropy change is checked (entropy_excess); the relaxed
+// values do not depend on DIAG.
+template <class Sys, class R, int OM, bool DIAG>
 __device__ __forceinline__ void relax_cell(const ParamsR<R> &P, R *f, int kind, bool &fallback, bool &increase,
-                                           R &omega_used)
+                                           R &omega_used, float &excess)
 {
     constexpr int Q = Sys::Q, M = Sys::M;
     R u[M], feq[Q * M];
     moments_target<Sys, R>(P, f, u, feq);
     fallback = false;
     increase = false;
+    excess = 0.0f;
     if (kind == KIND_PROJECT) {  // R_1: projection on the equilibrium (Section 6.1)
         omega_used = R(1);
 #pragma unroll
@@ -101,17 +243,16 @@ __device__ __forceinline__ void relax_cell(const ParamsR<R> &P, R *f, int kind, 
 #pragma unroll
     for (int i = 0; i < Q * M; ++i) delta[i] = feq[i] - f[i];
     R w = P.omega;
-    if constexpr (ENTROPIC && !Sys::LINEAR) {
+    if constexpr (OM != OM_FIXED && !Sys::LINEAR) {
         typename Sys::template Ctx<R> cx;
         Sys::template prepare<R>(P, u, delta, cx);
         w = entropic_omega<Sys, R>(P, cx, fallback);
+        if constexpr (OM == OM_MIXED) w = mixed_omega<Sys, R>(P, u, delta, w, fallback);
         if constexpr (DIAG) {
-            // per-cell check of Section 4: Sigma(R f) - Sigma(f) = F(omega - 1) <= 0
-            R B1, d1, B0, d0;
-            if (Sys::template eval<R>(P, cx, w - R(1), B1, d1) && Sys::template eval<R>(P, cx, R(-1), B0, d0))
-                increase = (B1 - B0) > R(64) * R(sizeof(R) == 4 ? 1.2e-7 : 2.3e-16) * B0;
+            excess = entropy_excess<Sys, R>(P, u, delta, w);
+            increase = entropy_increase<R, OM>(excess);
         }
-    } else if constexpr (ENTROPIC) {
+    } else if constexpr (OM != OM_FIXED) {
         w = R(2);  // quadratic kinetic entropies: omega* = 2 exactly (Proposition 2)
     }
     omega_used = w;
@@ -120,7 +261,7 @@ __device__ __forceinline__ void relax_cell(const ParamsR<R> &P, R *f, int kind, 
 }
 
 // Fused stage: pull-shift by sh (transport, eq. transportPhase) then relax.
-template <class Sys, int DIM, class R, bool ENTROPIC, bool DIAG>
+template <class Sys, int DIM, class R, int OM, bool DIAG>
 __global__ void __launch_bounds__(kBlock) k_stage(StageArgs<R> a, ParamsR<R> P)
 {
     constexpr int Q = Sys::Q, M = Sys::M;
@@ -129,7 +270,7 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageArgs<R> a, ParamsR<R> P)
     const bool valid = x < a.nx;
     R f[Q * M];
     bool fb = false, inc = false;
-    R w = R(1);
+    DiagAcc acc;
     if (valid) {
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
@@ -137,25 +278,18 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageArgs<R> a, ParamsR<R> P)
 #pragma unroll
             for (int m = 0; m < M; ++m) f[k * M + m] = a.fin[(int64_t)(k * M + m) * a.ncell + s];
         }
-        relax_cell<Sys, R, ENTROPIC, DIAG>(P, f, a.kind, fb, inc, w);
+        R w;
+        float ex;
+        relax_cell<Sys, R, OM, DIAG>(P, f, a.kind, fb, inc, w, ex);
+        if constexpr (DIAG) acc.add(float(w), ex);
         const int64_t o = y * a.nx + x;
 #pragma unroll
         for (int i = 0; i < Q * M; ++i) a.fout[(int64_t)i * a.ncell + o] = f[i];
     }
-    if constexpr (ENTROPIC && !Sys::LINEAR) warp_count(valid && fb, &a.cnt->fallbacks);
+    if constexpr (OM != OM_FIXED && !Sys::LINEAR) warp_count(valid && fb, &a.cnt->fallbacks);
     if constexpr (DIAG) {
         warp_count(valid && inc, &a.cnt->entropy_increases);
-        float wf = valid ? float(w) : 1.0f;
-        float wmin = wf, wmax = wf;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            wmin = fminf(wmin, __shfl_xor_sync(0xffffffffu, wmin, o));
-            wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicMin(&a.cnt->omega_min_bits, __float_as_uint(wmin));
-            atomicMax(&a.cnt->omega_max_bits, __float_as_uint(wmax));
-        }
+        acc.flush(a.cnt);
     }
 }
 
@@ -193,7 +327,7 @@ template <class R> struct BulkArgs {
     Counters *cnt;
 };
 
-template <class Sys, class R, bool ENTROPIC>
+template <class Sys, class R, int OM, bool DIAG>
 __global__ void __launch_bounds__(kRowThreads) k_stage_bulk(BulkArgs<R> a, ParamsR<R> P)
 {
     constexpr int Q = Sys::Q, M = Sys::M, NP = Q * M;
@@ -269,6 +403,7 @@ __global__ void __launch_bounds__(kRowThreads) k_stage_bulk(BulkArgs<R> a, Param
         if (threadIdx.x == 0) atomicAdd(&a.cnt->copy_timeouts, 1ull);
         return;
     }
+    DiagAcc acc;
     for (int j0 = 0; j0 < kRowTile; j0 += kRowThreads) {  // same trip count for every thread
         const int j = j0 + threadIdx.x;
         const bool valid = j < T;
@@ -278,13 +413,17 @@ __global__ void __launch_bounds__(kRowThreads) k_stage_bulk(BulkArgs<R> a, Param
 #pragma unroll
             for (int p = 0; p < NP; ++p) f[p] = sm[(int64_t)p * a.slot + s_off[p] + j];
             R w;
-            relax_cell<Sys, R, ENTROPIC, false>(P, f, a.kind, fb, inc, w);
+            float ex;
+            relax_cell<Sys, R, OM, DIAG>(P, f, a.kind, fb, inc, w, ex);
+            if constexpr (DIAG) acc.add(float(w), ex);
             const int64_t o = y * a.nx + x0 + j;
 #pragma unroll
             for (int p = 0; p < NP; ++p) a.fout[(int64_t)p * a.ncell + o] = f[p];
         }
-        if constexpr (ENTROPIC && !Sys::LINEAR) warp_count(fb, &a.cnt->fallbacks);
+        if constexpr (OM != OM_FIXED && !Sys::LINEAR) warp_count(fb, &a.cnt->fallbacks);
+        if constexpr (DIAG) warp_count(inc, &a.cnt->entropy_increases);
     }
+    if constexpr (DIAG) acc.flush(a.cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -313,7 +452,7 @@ template <class R> struct FusedArgs {
     int nrec;
 };
 
-template <class Sys, class R, bool ENTROPIC, bool RECORD = false>
+template <class Sys, class R, int OM, bool RECORD = false, bool DIAG = false>
 __global__ void __launch_bounds__(kFusedBlock, sizeof(R) == 4 ? 4 : 2)
     k_step1d(FusedArgs<R> a, StageList sl, ParamsR<R> P)
 {
@@ -336,6 +475,7 @@ __global__ void __launch_bounds__(kFusedBlock, sizeof(R) == 4 ? 4 : 2)
 #pragma unroll
     for (int k = 0; k < Q; ++k) off[k] = 0;
     int moved = 0;  // sum of |shift| over the stages so far
+    DiagAcc acc;
     for (int st = 0; st < sl.n; ++st) {
         const int s = sl.shift[st], kind = sl.kind[st];
 #pragma unroll
@@ -364,15 +504,21 @@ __global__ void __launch_bounds__(kFusedBlock, sizeof(R) == 4 ? 4 : 2)
 #pragma unroll
                     for (int m = 0; m < M; ++m) f[k * M + m] = sm[(k * M + m) * W + slot[k]];
                 R w;
-                relax_cell<Sys, R, ENTROPIC, false>(P, f, kind, fb, inc, w);
-                // only cells of the final tile count towards the fallback counter
-                fb = fb && j >= H && j < H + T;
+                float ex;
+                relax_cell<Sys, R, OM, DIAG>(P, f, kind, fb, inc, w, ex);
+                // only cells of the final tile count towards the counters (each cell-stage once)
+                const bool in_tile = j >= H && j < H + T;
+                fb = fb && in_tile;
+                inc = inc && in_tile;
+                if constexpr (DIAG)
+                    if (in_tile) acc.add(float(w), ex);
 #pragma unroll
                 for (int k = 0; k < Q; ++k)
 #pragma unroll
                     for (int m = 0; m < M; ++m) sm[(k * M + m) * W + slot[k]] = f[k * M + m];
             }
-            if constexpr (ENTROPIC && !Sys::LINEAR) warp_count(fb, &a.cnt->fallbacks);
+            if constexpr (OM != OM_FIXED && !Sys::LINEAR) warp_count(fb, &a.cnt->fallbacks);
+            if constexpr (DIAG) warp_count(inc, &a.cnt->entropy_increases);
         }
         __syncthreads();
         if constexpr (RECORD) {
@@ -391,6 +537,7 @@ __global__ void __launch_bounds__(kFusedBlock, sizeof(R) == 4 ? 4 : 2)
             }
         }
     }
+    if constexpr (DIAG) acc.flush(a.cnt);
     // write the exact tile
     for (int j = threadIdx.x; j < T; j += blockDim.x) {
 #pragma unroll
@@ -417,7 +564,7 @@ __global__ void __launch_bounds__(kFusedBlock, sizeof(R) == 4 ? 4 : 2)
 // equilibrium, fallback cells (omega = 1) and quadratic entropies have a
 // locally constant omega and no such term.
 // ---------------------------------------------------------------------------
-template <class Sys, class R, bool ENTROPIC>
+template <class Sys, class R, int OM>
 __device__ __forceinline__ void relax_adjoint(const ParamsR<R> &P, const R *f, const R *gout, int kind, R *gin)
 {
     constexpr int Q = Sys::Q, M = Sys::M;
@@ -449,20 +596,21 @@ __device__ __forceinline__ void relax_adjoint(const ParamsR<R> &P, const R *f, c
     bool varying = false;
     typename Sys::template Ctx<R> cx;
     R Dm[Q * M];  // dual deviations at t = -1, from the root-find's own evaluation there
-    if constexpr (ENTROPIC && !Sys::LINEAR) {
+    if constexpr (OM != OM_FIXED && !Sys::LINEAR) {
         Sys::template prepare<R>(P, u, delta, cx);
         bool fb = false;
         R E0 = R(0);
         w = entropic_omega<Sys, R>(P, cx, fb, Dm, &E0);
+        if constexpr (OM == OM_MIXED) w = mixed_omega<Sys, R>(P, u, delta, w, fb);
         varying = !fb && E0 > R(0);
-    } else if constexpr (ENTROPIC) {
+    } else if constexpr (OM != OM_FIXED) {
         w = R(2);
     }
 #pragma unroll
     for (int k = 0; k < Q; ++k)
 #pragma unroll
         for (int n = 0; n < M; ++n) gin[k * M + n] = (R(1) - w) * gout[k * M + n] + w * a[n];
-    if constexpr (ENTROPIC && !Sys::LINEAR) {
+    if constexpr (OM != OM_FIXED && !Sys::LINEAR) {
         if (varying) {
             const R t = w - R(1);
             R Dt[Q * M], B, dB;
@@ -495,7 +643,7 @@ __device__ __forceinline__ void relax_adjoint(const ParamsR<R> &P, const R *f, c
 // Adjoint of a fused stage f_out(x) = R(f_in(src_k(x))): the cotangent of the
 // stage input at src_k(x) is (J_R(x)^T g_out(x))_k (the reverse shift; src_k is
 // a bijection, so every input cell receives exactly one contribution).
-template <class Sys, int DIM, class R, bool ENTROPIC>
+template <class Sys, int DIM, class R, int OM>
 __global__ void __launch_bounds__(kBlock) k_adjoint_stage(const R *__restrict__ fin, const R *__restrict__ gout,
                                                           R *__restrict__ gin, int64_t nx, int64_t ny, Shift sh,
                                                           int kind, ParamsR<R> P)
@@ -516,7 +664,7 @@ __global__ void __launch_bounds__(kBlock) k_adjoint_stage(const R *__restrict__ 
             go[k * M + m] = gout[(int64_t)(k * M + m) * ncell + o];
         }
     }
-    relax_adjoint<Sys, R, ENTROPIC>(P, f, go, kind, gi);
+    relax_adjoint<Sys, R, OM>(P, f, go, kind, gi);
 #pragma unroll
     for (int k = 0; k < Q; ++k)
 #pragma unroll
@@ -583,12 +731,13 @@ template <class R> struct BatchArgs {
     Counters *cnt;
 };
 
-template <class Sys, class R, bool ENTROPIC>
+template <class Sys, class R, int OM, bool DIAG>
 __global__ void __launch_bounds__(kBlock) k_batch_step(BatchArgs<R> a, StageList sl, ParamsR<R> P)
 {
     constexpr int Q = Sys::Q, M = Sys::M;
     cg::grid_group grid = cg::this_grid();
     int side = a.side;
+    DiagAcc acc;
     for (int st = 0; st < sl.n; ++st) {
         const R *__restrict__ fin = a.pool[side];
         R *__restrict__ fout = a.pool[side ^ 1];
@@ -619,17 +768,21 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchArgs<R> a, StageList
                         for (int m = 0; m < M; ++m) f[k * M + m] = fi[(int64_t)(k * M + m) * ncell + src];
                     }
                     R wv;
-                    relax_cell<Sys, R, ENTROPIC, false>(P, f, kind, fb, inc, wv);
+                    float ex;
+                    relax_cell<Sys, R, OM, DIAG>(P, f, kind, fb, inc, wv, ex);
+                    if constexpr (DIAG) acc.add(float(wv), ex);
                     const int64_t o = y * I.nx + x;
 #pragma unroll
                     for (int i = 0; i < Q * M; ++i) fo[(int64_t)i * ncell + o] = f[i];
                 }
-                if constexpr (ENTROPIC && !Sys::LINEAR) warp_count(fb, &a.cnt->fallbacks);
+                if constexpr (OM != OM_FIXED && !Sys::LINEAR) warp_count(fb, &a.cnt->fallbacks);
+                if constexpr (DIAG) warp_count(inc, &a.cnt->entropy_increases);
             }
         }
         side ^= 1;
         grid.sync();
     }
+    if constexpr (DIAG) acc.flush(a.cnt);
 }
 
 // f_k = f^eq_k(u0) (Section 3.1) with the domain check of Section 1.2.

@@ -36,10 +36,10 @@ struct FusedLaunch {
 };
 
 // temporally blocked 1D step (several stages in shared memory); 1D families only
-cudaError_t launch_fused1d(int family, bool fp64, bool entropic, const FusedLaunch &L);
+cudaError_t launch_fused1d(int family, bool fp64, int om, bool diag, const FusedLaunch &L);
 
 // fused pull-shift + relaxation stage
-cudaError_t launch_stage(int family, bool fp64, bool entropic, bool diag, const StageLaunch &L);
+cudaError_t launch_stage(int family, bool fp64, int om, bool diag, const StageLaunch &L);
 // f = f^eq(u0) with the domain check
 cudaError_t launch_init_eq(int family, bool fp64, const double *u0, void *f, int64_t ncell, const Params &P,
                            Counters *cnt, cudaStream_t st);
@@ -71,7 +71,7 @@ struct AdjointLaunch {
 };
 
 // reverse-mode stage (reverse shift + transposed relaxation Jacobian)
-cudaError_t launch_adjoint_stage(int family, bool fp64, bool entropic, const AdjointLaunch &L);
+cudaError_t launch_adjoint_stage(int family, bool fp64, int om, const AdjointLaunch &L);
 // cotangent of the distributions from the cotangent of the moments (pending shift sh)
 cudaError_t launch_adjoint_readout(int dim, bool fp64, const double *lam, void *g, int64_t nx, int64_t ny, int M,
                                    const Shift &sh, cudaStream_t st);
@@ -93,9 +93,9 @@ struct BatchLaunch {
 };
 
 // one composite step of every instance of a 2D batch (cooperative, grid.sync between stages)
-cudaError_t launch_batch_step(int family, bool fp64, bool entropic, const BatchLaunch &L);
+cudaError_t launch_batch_step(int family, bool fp64, int om, bool diag, const BatchLaunch &L);
 // resident blocks per SM of that kernel (0 if the family has no batched kernel)
-int batch_blocks_per_sm(int family, bool fp64, bool entropic);
+int batch_blocks_per_sm(int family, bool fp64, int om, bool diag);
 
 int totals_blocks();
 

@@ -33,6 +33,8 @@ std::mutex g_mutex;
 double *g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch on the current device (set-up once per device).
+// The address is cached for the life of the process: it is not looked up again
+// after cudaDeviceReset or any other teardown of the device's primary context.
 eslbm_status scratch_for_current_device(double **out)
 {
     int dev = -1;
@@ -59,6 +61,16 @@ extern "C" eslbm_status eslbm_read_totals_noalloc(const eslbm_config *cfg, const
     if (!f || !out || ((uintptr_t)f & 15u)) return ESLBM_ERR_ARG;
     const int nv = 2 + (int)sz.M;
     if (nv > kMaxTotals || totals_blocks() * kMaxTotals + kMaxTotals > kScratchDoubles) return ESLBM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!out_on_device) {
+        // the host copy ends with a stream synchronization, which stream capture forbids
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+            (void)cudaGetLastError();  // leave no error behind for later launches
+            return ESLBM_ERR_ARG;
+        }
+        if (cs != cudaStreamCaptureStatusNone) return ESLBM_ERR_ARG;
+    }
     double *scratch = nullptr;
     s = scratch_for_current_device(&scratch);
     if (s != ESLBM_OK) return s;
@@ -76,7 +88,6 @@ extern "C" eslbm_status eslbm_read_totals_noalloc(const eslbm_config *cfg, const
         if (r < 0) r += n;
         sh.roff[k] = r;
     }
-    cudaStream_t st = (cudaStream_t)stream;
     double *partials = scratch;
     double *final_totals = scratch + (size_t)kMaxTotals * (size_t)totals_blocks();
     double *dst = out_on_device ? out : final_totals;

@@ -630,14 +630,16 @@ __device__ R entropic_omega(const ParamsR<R> &P, const typename Sys::template Ct
         if (tm > lo && tm < hi) {
             if (fabs(tm - R(1)) <= R(0.25)) {
                 // The four values fix the quartic model with one datum to spare.  Its
-                // residual r = (B'(1) + B'(-1)) - 3 (B(1) - B(-1)) is 4 c5 + 14 c7 + ... for
-                // B(t) = sum_n c_n t^n, the odd content the model misses (the even content
-                // vanishes at t = 1 in F).  When r is at the rounding level of B the model root
-                // is as good as an exact evaluation at it would certify: return it, lowered by
-                // the model's error bound over F'(tm) so that F stays <= 0.
-                // The even content beyond the model, c6 (t^6 - 1) + ..., is not measured; near
-                // t = 1 it is about 6 c6 (t - 1), and c6 is estimated from the decay of the
-                // series, c6 ~ c4^2 / c2, which must be at the rounding level too.
+                // residual r = (B'(1) + B'(-1)) - 3 (B(1) - B(-1)) is the sum over odd n of
+                // 2 (n - 3) c_n = 4 c5 + 8 c7 + ... for B(t) = sum_n c_n t^n, the odd content the
+                // model misses.  When r is at the rounding level of B the model root is as good
+                // as an exact evaluation at it would certify: return it, lowered by the model's
+                // error bound over F'(tm) so that F stays <= 0.
+                // The even content beyond the model is not measured: the model takes
+                // b2 = c2 - c6, b4 = c4 + 2 c6, which leaves c6 t^2 (t^2 - 1)^2 + ..., about
+                // 4 c6 (t - 1)^2 near t = 1.  The bound used, 6 c6 |t - 1| with c6 estimated from
+                // the decay of the series, c6 ~ c4^2 / c2, over-bounds that term for |t - 1| <= 1/4
+                // and must be at the rounding level too.
                 const R r = (dBp + dEm) - R(3) * (Bp - Em);
                 const R eps = sizeof(R) == 4 ? R(1.1920929e-7) : R(2.220446049250313e-16);
                 const R tol = R(64) * eps * (Bp + Em);

@@ -17,7 +17,9 @@ OK, ERR_ARG, ERR_DOMAIN, ERR_CUDA, ERR_NAN, ERR_UNSUPPORTED, WARN_OMEGA_FALLBACK
 LINEAR, BURGERS, SHALLOW_WATER, EULER = 0, 1, 2, 3
 SYSTEMS = {"linear": LINEAR, "burgers": BURGERS, "sw": SHALLOW_WATER, "shallow_water": SHALLOW_WATER,
            "euler": EULER}
-FP32, FP64 = 0, 1
+FP32, FP64, FP32_MIXED = 0, 1, 2
+PRECISIONS = {"fp32": FP32, "fp64": FP64, "float64": FP64, "fp32_mixed": FP32_MIXED}
+BLOCKING_AUTO, BLOCKING_OFF = 0, 1
 OMEGA_FIXED, OMEGA_ENTROPIC = 0, 1
 SCHEMES = {"I": 1, "II": 2, "III": 3, "IV": 4, "plain": 5, "B": 6}
 RELAX_MAIN, RELAX_PROJECT = 0, 1
@@ -39,7 +41,8 @@ class Config(ctypes.Structure):
                 ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("V", ctypes.c_double),
                 ("omega", ctypes.c_double), ("a", ctypes.c_double * 2), ("c", ctypes.c_double * 2),
                 ("g", ctypes.c_double), ("gamma", ctypes.c_double), ("t_max", ctypes.c_double),
-                ("diagnostics", ctypes.c_int32), ("shifted", ctypes.c_int32), ("u_ref", ctypes.c_double * 4)]
+                ("diagnostics", ctypes.c_int32), ("shifted", ctypes.c_int32), ("u_ref", ctypes.c_double * 4),
+                ("blocking", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Sizes(ctypes.Structure):
@@ -52,7 +55,7 @@ class Sizes(ctypes.Structure):
 class Diagnostics(ctypes.Structure):
     _fields_ = [("relaxations", ctypes.c_uint64), ("fallbacks", ctypes.c_uint64),
                 ("entropy_increases", ctypes.c_uint64), ("omega_min", ctypes.c_double),
-                ("omega_max", ctypes.c_double)]
+                ("omega_max", ctypes.c_double), ("entropy_excess_max", ctypes.c_double)]
 
 
 class BatchSizes(ctypes.Structure):
@@ -131,12 +134,14 @@ class EslbmError(RuntimeError):
 
 
 def make_config(dim, system, nx, ny=1, V=1.0, precision="fp32", omega_mode="fixed", omega=2.0, scheme="I",
-                a=(0.0, 0.0), c=(1.0, 1.0), g=1.0, gamma=1.4, t_max=3.0, kappa=1, diagnostics=False, u_ref=None):
-    """Configuration of one lattice; u_ref (conserved values) selects the shifted storage."""
+                a=(0.0, 0.0), c=(1.0, 1.0), g=1.0, gamma=1.4, t_max=3.0, kappa=1, diagnostics=False, u_ref=None,
+                blocking=True):
+    """Configuration of one lattice; u_ref (conserved values) selects the shifted storage; precision is
+    "fp32", "fp64" or "fp32_mixed"; blocking=False runs one launch per fused stage."""
     cfg = Config()
     cfg.dim = int(dim)
     cfg.system = SYSTEMS[system] if isinstance(system, str) else int(system)
-    cfg.precision = FP64 if precision in ("fp64", "float64", FP64) else FP32
+    cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     cfg.omega_mode = OMEGA_ENTROPIC if omega_mode in ("entropic", OMEGA_ENTROPIC) else OMEGA_FIXED
     cfg.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     cfg.kappa = int(kappa)
@@ -151,6 +156,7 @@ def make_config(dim, system, nx, ny=1, V=1.0, precision="fp32", omega_mode="fixe
     cfg.t_max = float(t_max)
     cfg.diagnostics = 1 if diagnostics else 0
     cfg.shifted = 0 if u_ref is None else 1
+    cfg.blocking = BLOCKING_AUTO if blocking else BLOCKING_OFF
     if u_ref is not None:
         for i, v in enumerate(u_ref):
             cfg.u_ref[i] = float(v)
@@ -296,7 +302,7 @@ class Simulation:
         self._check(st)
         return {"relaxations": d.relaxations, "fallbacks": d.fallbacks,
                 "entropy_increases": d.entropy_increases, "omega_min": d.omega_min, "omega_max": d.omega_max,
-                "status": st}
+                "entropy_excess_max": d.entropy_excess_max, "status": st}
 
     def reset_diagnostics(self):
         return self._check(lib().eslbm_reset_diagnostics(self.h))
@@ -432,7 +438,8 @@ class Batch:
         d = Diagnostics()
         st = lib().eslbm_batch_get_diagnostics(self.h, ctypes.byref(d))
         self._check(st)
-        return {"fallbacks": d.fallbacks, "status": st}
+        return {"fallbacks": d.fallbacks, "entropy_increases": d.entropy_increases, "omega_min": d.omega_min,
+                "omega_max": d.omega_max, "entropy_excess_max": d.entropy_excess_max, "status": st}
 
     def gradient(self, u0, dJ_duT, n, K=50):
         """Per-instance dJ/du0 (flat float64 CUDA tensor; inputs flat or per-instance lists)."""

@@ -33,7 +33,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_abi_version_and_status_strings(L):
-    assert L.eslbm_abi_version() == 2
+    assert L.eslbm_abi_version() == 3
     for s in (0, 1, 2, 3, 4, 5, 100, 77):
         assert L.eslbm_status_string(s)
 
@@ -73,6 +73,7 @@ def test_query_sizes(L):
     (dict(system="sw", V=4.0, g=9.81, u_ref=(-1.0, 0.0)), eslbm.ERR_DOMAIN),  # negative reference depth
     (dict(system="sw", V=4.0, g=9.81, u_ref=(1.0, 5.0)), eslbm.ERR_DOMAIN),   # |v| + sqrt(g h) > V
     (dict(system="burgers", V=1.0, u_ref=(1.2,)), eslbm.ERR_DOMAIN),          # |u| >= V (D1Q2)
+    (dict(precision=3), eslbm.ERR_ARG),
 ])
 def test_query_rejects(L, bad, status):
     cfg = q(**bad)
@@ -90,6 +91,42 @@ def test_shifted_reference_is_accepted(L):
     with pytest.raises(eslbm.EslbmError) as e:
         eslbm.query(bad)
     assert e.value.status == eslbm.ERR_ARG
+
+
+def test_mixed_precision_and_blocking_fields(L):
+    """FP32_MIXED stores FP32 (same buffer sizes as FP32); blocking takes AUTO or OFF only."""
+    a = eslbm.query(q(system="sw", V=4.0, g=9.81, precision="fp32", omega_mode="entropic"))
+    b = eslbm.query(q(system="sw", V=4.0, g=9.81, precision="fp32_mixed", omega_mode="entropic"))
+    assert a.state_bytes == b.state_bytes == 4 * 256 * 4
+    assert eslbm.query(q(blocking=False)).planes == 2
+    bad = q()
+    bad.blocking = 2
+    with pytest.raises(eslbm.EslbmError) as e:
+        eslbm.query(bad)
+    assert e.value.status == eslbm.ERR_ARG
+
+
+def test_structs_match_header(L, tmp_path):
+    """The ctypes mirrors of the ABI structs have the C layout: sizes and field offsets printed by
+    a C program compiled against include/eslbm.h."""
+    import subprocess
+    structs = {"eslbm_config": eslbm.Config, "eslbm_sizes": eslbm.Sizes, "eslbm_diagnostics": eslbm.Diagnostics,
+               "eslbm_batch_sizes": eslbm.BatchSizes}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "eslbm.h"', 'int main(void) {']
+    for cname, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for cname, cls in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(got["%s.%s" % (cname, f)]) == getattr(cls, f).offset, (cname, f)
 
 
 def test_entropic_euler_is_unsupported(L):

@@ -145,3 +145,44 @@ def test_step_lengths():
     m = O.Model(1, "burgers", 8, V=1.0)
     assert O.step_length(m, "I") == 24 and O.step_length(m, "plain") == 1
     assert O.step_length(m, "B") == 4
+
+
+@pytest.mark.parametrize("aV", [0.2, 0.45, 0.7])
+def test_scheme_b_symbol_is_second_order(aV):
+    """Section 6.3, scheme (B) = R_1 T(dt/4) R_2 T(dt/2) R_2 T(dt/4) with dt = 4 dx / V.  On linear
+    D1Q2 its symbol has rank one (R_1 is the last operator) and the non-zero eigenvalue, worked out
+    from the operator definitions (T(s) multiplies f_+ by exp(-i s xi dx) and f_- by exp(i s xi dx),
+    R_2 f = 2 f^eq(u) - f, R_1 f = f^eq(u)), is
+        z = exp(-i a xi dt) + a (V^2 - a^2) / 24 * (i (xi dt)^3 + a (xi dt)^4) + O((xi dt)^5)
+    (V = 1 here): a second-order scheme whose leading error vanishes at a = 0 and |a| = V.  A wrong
+    shift (1, 2, 1 cells) or a relaxation left out changes the cubic coefficient."""
+    V, N = 1.0, 400
+    for j in (1, 2):
+        A = amplification(aV, N, j, scheme="B", V=V)
+        ev = np.linalg.eigvals(A)
+        assert min(np.abs(ev)) < 1e-12
+        z = ev[np.argmax(np.abs(ev))]
+        xdt = 2 * np.pi * j / N * 4 / V
+        k3 = 1j * aV * (V ** 2 - aV ** 2) / 24
+        k4 = aV ** 2 * (V ** 2 - aV ** 2) / 24
+        d = z - np.exp(-1j * aV * xdt)
+        assert abs(d.imag / xdt ** 3 - k3.imag) < 2e-2 * abs(k3)
+        assert abs(d.real / xdt ** 4 - k4) < 5e-2 * abs(k4)
+
+
+@pytest.mark.parametrize("system,kw", [("burgers", dict(V=2.0)), ("sw", dict(V=4.0, g=1.0))])
+def test_scheme_b_ends_with_the_projection(system, kw):
+    """Scheme (B) applies R_1 last (Section 6.3: one basic brick plus a relaxation on the equilibrium),
+    so the distributions after every step are at equilibrium, f = f^eq(u), whatever the initial data.
+    A symbol test cannot see where R_1 sits (R_1 A and A R_1 share their non-zero eigenvalue); this
+    one fails if R_1 is moved."""
+    N = 64
+    m = O.Model(1, system, N, **kw)
+    u0 = inputs.sw_random_1d(N, seed=4) if system == "sw" else inputs.random_scalar_1d(N, seed=4)
+    f = inputs.perturb(O.init_equilibrium(m, u0), seed=5, scale=0.02)
+    f_eq0 = O.init_equilibrium(m, O.moments(m, f))
+    assert np.abs(f - f_eq0).max() > 1e-4  # the start is off equilibrium
+    for _ in range(3):
+        O.composite_steps(m, f, 1, scheme="B")
+        f_eq = O.init_equilibrium(m, O.moments(m, f))
+        np.testing.assert_allclose(f, f_eq, rtol=0, atol=1e-14)

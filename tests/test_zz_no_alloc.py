@@ -75,3 +75,40 @@ def test_noalloc_rejects_bad_arguments():
     with pytest.raises(eslbm.EslbmError) as e:
         eslbm.read_totals_noalloc(bad, buf.data_ptr(), 0, out.ctypes.data, 0, None)
     assert e.value.status == eslbm.ERR_ARG
+
+
+def test_noalloc_totals_in_a_captured_graph():
+    """The reason the call exists: totals recorded inside a CUDA graph capture (where no memory can
+    be allocated) and replayed.  The set-up call comes first, outside the capture; during capture a
+    host output is refused (it would need a stream synchronization) and leaves the capture intact."""
+    cfg = eslbm.make_config(1, "sw", 2048, V=4.0, g=9.81, precision="fp32", omega_mode="entropic")
+    sim = eslbm.Simulation(cfg)
+    sim.init_equilibrium(inputs.sw_random_1d(2048, seed=11))
+    sim.step(1)
+    ref = sim.totals()
+    f_logical = sim.distributions(host=True)
+    sim.close()
+    phys = torch.from_numpy(physical_from_logical(f_logical, cfg, 0)).to(torch.float32).cuda()
+    out = torch.zeros(len(ref), dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        eslbm.read_totals_noalloc(cfg, phys.data_ptr(), 0, out.data_ptr(), 1, side.cuda_stream)  # set-up
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    host = np.empty_like(ref)
+    with torch.cuda.graph(graph):
+        st = torch.cuda.current_stream().cuda_stream
+        with pytest.raises(eslbm.EslbmError) as e:
+            eslbm.read_totals_noalloc(cfg, phys.data_ptr(), 0, host.ctypes.data, 0, st)
+        assert e.value.status == eslbm.ERR_ARG
+        eslbm.read_totals_noalloc(cfg, phys.data_ptr(), 0, out.data_ptr(), 1, st)
+    for _ in range(2):  # two replays in a row on the shared scratch
+        out.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=1e-12)
+    # the graph reads the buffer at replay time: new contents, new totals
+    phys.mul_(0.5)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert abs(out[2].item() - 0.5 * ref[2]) <= 1e-9 * abs(ref[2])
