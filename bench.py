@@ -1,20 +1,26 @@
 #!/usr/bin/env python3
 """Throughput of the fourth-order entropy-stable composite step on GB300.
 
-Workload: 1D shallow water (h, hu), g = 9.81, vectorial D1Q2 per conserved
-variable (4 distributions per cell), periodic, h0 = 1 + 0.1 sin(2 pi x), u0 = 0,
-N = 2^20 cells, V = 4, entropic relaxation parameter, FP32 distributions, run
-to t = 0.05 (8738 composite steps of 18 fused stages).  One timed "step" is one
-whole solve through the C ABI: init at equilibrium from the device-resident
-conserved fields, the composite steps, and the readback of the moments and of
-the double-precision entropy / mass totals.
+Headline workload: 2D compressible Euler (rho, rho u, rho v, E), gamma = 1.4,
+vectorial D2Q4 per conserved variable (16 FP32 distributions per cell),
+periodic 8192 x 8192, isentropic vortex (strength 5, background rho = p = 1,
+velocity (1, 1)) on [0, 10]^2, V = 8, scheme I with omega = 2, 200 composite
+steps of 18 fused stages.  One timed "step" is one whole solve through the C
+ABI: init at equilibrium from the device-resident conserved fields, the
+composite steps, and the readback of the moments and of the double-precision
+totals.  value = site updates per second (cells x composite steps / time),
+summed over ranks; with several GPUs every rank solves its own replica (the
+path has no exchange between replicas).
 
-value = site updates per second (cells x composite steps / time), summed over
-ranks.  With several GPUs every rank solves its own replica (the path has no
-exchange between replicas).
+The other workloads of the path are reported in the same line: 1D shallow
+water at N = 2^20 to t = 0.05 (entropic omega, FP32), 2D Burgers 4096^2 for
+2000 steps (entropic, past the shock), Euler 4096^2 random-interface Riemann
+data (scheme III), 64 uneven batched 2D shallow-water instances for 500 steps
+with the reverse mode, FP32 against FP64, the precision split, and the FP64
+CPU oracle on the host cores.
 
---impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload on the host cores.
+--impl reference times the FP64 CPU oracle (OpenMP over the host cores) on a
+bounded sample of the headline workload.
 """
 import argparse
 import json
@@ -33,20 +39,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "composite-step site updates/s + HBM GB/s fraction; FP32 vs FP64 at stated L2 error"
 UNIT = "site_updates/s"
-N_CELLS = 1 << 20
-V, G, T_FINAL = 4.0, 9.81, 0.05
-U_REF = (1.0, 0.0)  # reference state of the shifted FP32 storage: the background depth at rest
-BATCH_V = 8.0  # lattice velocity of the batched 2D shallow-water instances: sqrt(9.81 x 1.05) < V/2
-L2_FLUSH_BYTES = 512 << 20
-# FP32 roofline of the dominant kernel (the fused composite step k_step1d, entropic shallow water):
-# 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz; and the FP32 operations of one cell-stage
-# (FADD + FMUL + 2 FFMA counted by ncu on this workload: 7.98e9 flops per launch over the 19.25e6
-# cell-stages a launch computes, 607 blocks x 31716).  The kernel is bound by instruction issue: 641 thread instructions
-# per cell-stage against 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz.
+
+# headline: Euler 8192^2 isentropic vortex, scheme I, omega = 2, FP32
+EULER_N, EULER_V, EULER_GAMMA, EULER_STEPS = 8192, 8.0, 1.4, 200
+# 1D shallow water (the 1D workload), 2D Burgers, batched shallow water
+SW_N, SW_V, G, SW_T = 1 << 20, 4.0, 9.81, 0.05
+SW_UREF = (1.0, 0.0)  # reference state of the shifted FP32 storage: the background depth at rest
+BURGERS_N, BURGERS_V, BURGERS_STEPS = 4096, 3.0, 2000
+RIEMANN_N, RIEMANN_STEPS = 4096, 500
+BATCH_V, BATCH_STEPS, BATCH_K = 8.0, 500, 50
+# FP32 ALU roofline of the 1D entropic kernel (an explanation next to the HBM model there):
+# 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz, 415 FP32 flops per cell-stage (ncu count)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FLOPS_PER_CELL_STAGE = 415.0
-ISSUE_PEAK_TINST = 152 * 4 * 32 * 2.07e9 / 1e12
-INST_PER_CELL_STAGE = 641.0
+SW_FLOPS_PER_CELL_STAGE = 415.0
 
 
 def parse():
@@ -55,13 +60,12 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--n", type=int, default=N_CELLS)
-    p.add_argument("--t-final", type=float, default=T_FINAL)
-    p.add_argument("--no-extras", action="store_true", help="skip the FP64 and CPU baseline legs")
-    p.add_argument("--leg", default=None, choices=["hbm2d", "batched", "fp32err"],
-                   help="run one secondary measurement alone and print its JSON (for profiling)")
-    p.add_argument("--hbm-steps", type=int, default=20, help="composite steps of the 2D streaming leg")
-    p.add_argument("--hbm-case", default=None, help="one case of the 2D streaming leg (default: all)")
+    p.add_argument("--n", type=int, default=EULER_N, help="headline grid (n x n)")
+    p.add_argument("--composite-steps", type=int, default=EULER_STEPS, help="headline composite steps per solve")
+    p.add_argument("--no-extras", action="store_true", help="headline only (no other workloads, no CPU baseline)")
+    p.add_argument("--leg", default=None,
+                   choices=["sw1d", "burgers2d", "riemann", "batched", "precision", "accuracy", "adjoint", "cpu"],
+                   help="run one secondary measurement alone and print its JSON")
     p.add_argument("--batch-count", type=int, default=64, help="instances of the batched leg")
     return p.parse_args()
 
@@ -140,94 +144,101 @@ def aggregate(total_ms, units_per_rank, dist=None, device=None):
     return world * units_per_rank / (total_ms * 1e-3), total_ms
 
 
+def hbm_roofline(bytes_per_site_update, site_updates, seconds, kernel, launches, extra=None):
+    """Per-stage traffic model of the path (every distribution read and written once per fused
+    stage, 2 q M b bytes per cell-stage, 18 cell-stages per site update) over the dominant kernel's
+    launches, timed back to back on one stream with CUDA events."""
+    peak, kind = peaks()
+    achieved = bytes_per_site_update * site_updates / seconds / 1e9
+    r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+         "traffic": None, "model": "per-stage: 18 x 2 q M b bytes per site update",
+         "bytes_per_site_update": bytes_per_site_update, "peak_source": kind, "kernel": kernel,
+         "launches": launches, "launch_us": seconds / max(launches, 1) * 1e6}
+    if extra:
+        r.update(extra)
+    return r
+
+
 # ---------------------------------------------------------------------------
-# reference arm / CPU baseline: the FP64 oracle on a bounded sample
+# the FP64 CPU oracle on bounded samples (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(n_cells=512, steps=1):
+def oracle_rate(workload, openmp):
+    """Site updates per second of the FP64 oracle on a bounded sample of a workload (about 10 s of
+    single-threaded work).  Returns (rate, seconds, sample description, threads)."""
     import oracle as O
     from paper_2403_13406_gb300 import inputs
-    m = O.Model(1, "sw", n_cells, V=V, g=G, omega_mode="entropic")
-    f = O.init_equilibrium(m, inputs.sw_sine_1d(n_cells, 1.0, 0.1))
+    used = O.set_openmp(openmp)
+    threads = (os.cpu_count() or 1) if (openmp and used) else 1
+    if openmp and used:
+        os.environ.setdefault("OMP_NUM_THREADS", str(threads))
+    if workload == "euler":
+        n, steps = (1024, 2) if (openmp and used) else (384, 2)
+        m = O.Model(2, "euler", n, n, V=EULER_V, gamma=EULER_GAMMA)
+        f = O.init_equilibrium(m, inputs.euler_vortex_2d(n, n))
+        desc = "Euler isentropic vortex %d^2, %d composite steps (scheme I, omega = 2)" % (n, steps)
+        cells = n * n
+    else:
+        n, steps = (1 << 15, 2) if (openmp and used) else (1 << 12, 2)
+        m = O.Model(1, "sw", n, V=SW_V, g=G, omega_mode="entropic")
+        f = O.init_equilibrium(m, inputs.sw_sine_1d(n, 1.0, 0.1))
+        desc = "1D shallow water N = %d, %d composite steps (entropic omega)" % (n, steps)
+        cells = n
     t0 = time.perf_counter()
     O.composite_steps(m, f, steps)
     dt = time.perf_counter() - t0
-    return n_cells * steps / dt, dt
+    O.set_openmp(False)
+    return cells * steps / dt, dt, desc, threads
 
 
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    n_cells = 512
     for _ in range(args.warmup):
-        oracle_sample(n_cells)
+        oracle_rate("euler", True)
     rates, times = [], []
+    desc, threads = "", 1
     for _ in range(args.steps):
-        r, dt = oracle_sample(n_cells)
+        r, dt, desc, threads = oracle_rate("euler", True)
         rates.append(r)
         times.append(dt)
-    value = n_cells * args.steps / sum(times)
-    sample = "oracle (FP64 C, single thread), 1 composite step of the 1D shallow-water workload on %d cells" % n_cells
+    value = statistics.mean(rates)
+    sample = "FP64 C oracle (OpenMP, %d threads): %s" % (threads, desc)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "sw1d_d1q2_entropic_n%d_t%g" % (args.n, args.t_final), "system": "shallow_water",
-                       "lattice": "D1Q2", "N": args.n, "V": V, "g": G, "t_final": args.t_final, "omega": "entropic",
-                       "N_sample": n_cells, "steps_per_sample": 1},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": headline_config(args.n, args.composite_steps),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+def headline_config(n, steps):
+    return {"workload": "euler2d_d2q4_vortex_n%d_steps%d" % (n, steps), "system": "euler", "lattice": "D2Q4",
+            "nx": n, "ny": n, "M": 4, "V": EULER_V, "gamma": EULER_GAMMA, "scheme": "I", "omega": "fixed 2",
+            "composite_steps": steps, "stages_per_step": 18, "precision": "fp32", "storage": "plain",
+            "initial_data": "isentropic vortex, strength 5, rho = p = 1, velocity (1, 1), on [0, 10]^2",
+            "l2": "inputs larger than L2 (4.3 GB per state buffer); no flush needed"}
+
+
 # ---------------------------------------------------------------------------
-# our arm
+# headline: Euler 8192^2
 # ---------------------------------------------------------------------------
 
-def main():
-    args = parse()
-    if args.impl == "reference":
-        reference_arm(args)
-        return
-    import torch
-    from paper_2403_13406_gb300 import eslbm, inputs
-    if args.leg:
-        torch.cuda.set_device(0)
-        dev = torch.device("cuda", 0)
-        stream = torch.cuda.Stream(device=dev)
-        leg = {"hbm2d": hbm2d_leg, "batched": batch_leg, "fp32err": fp32err_leg}[args.leg]
-        kw = ({"steps": args.hbm_steps, "only": args.hbm_case} if args.leg == "hbm2d" else
-              {"N": args.n, "t_final": args.t_final} if args.leg == "fp32err" else {"count": args.batch_count})
-        print(json.dumps(leg(torch, eslbm, inputs, stream, dev, **kw)), flush=True)
-        return
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        torch.cuda.set_device(0)
-    dev = torch.device("cuda", local if world > 1 else 0)
-    stream = torch.cuda.Stream(device=dev)
-
-    N = args.n
-    n_steps = inputs.steps_for(args.t_final, 1.0 / N, V)
-    cfg = eslbm.make_config(1, "sw", N, V=V, g=G, precision="fp32", omega_mode="entropic", u_ref=U_REF)
+def headline(torch, eslbm, inputs, stream, dev, args, world, dist, local):
+    n, n_steps = args.n, args.composite_steps
+    cfg = eslbm.make_config(2, "euler", n, n, V=EULER_V, gamma=EULER_GAMMA, precision="fp32", omega_mode="fixed")
     with torch.cuda.stream(stream):
         sim = eslbm.Simulation(cfg, stream=stream, device=dev)
         sim.use_graph(True)
-        u0_host = inputs.sw_sine_1d(N, 1.0, 0.1)
+        u0_host = inputs.euler_vortex_2d(n, n)
         u0 = torch.from_numpy(u0_host).to(dev)
-        u_out = torch.empty((sim.M, N), dtype=torch.float64, device=dev)
+        u_out = torch.empty((sim.M, n, n), dtype=torch.float64, device=dev)
         tot = torch.empty(2 + sim.M, dtype=torch.float64, device=dev)
-        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stages = int(sim.sizes.stages_per_step) * n_steps
-    launches_per_step = 1 + n_steps + 1 + 2  # init, one fused launch per composite step, gather, totals
+    sz = sim.sizes
+    launches_step = float(sz.launches_per_step)
 
     def solve(ev=None):
         sim.init_equilibrium(u0)
@@ -249,7 +260,6 @@ def main():
         clocks.start()
         evs = []
         for _ in range(args.steps):
-            flush.fill_(1.0)  # write > L2 between timed steps (outside the events)
             e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             e[0].record(stream)
             solve(ev=(e[1], e[2]))
@@ -260,157 +270,229 @@ def main():
         if dist:
             dist.barrier()
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
-    stage_ms = [e[1].elapsed_time(e[2]) / stages for e in evs]
-    value, total_ms = aggregate(sum(step_ms), N * n_steps * args.steps, dist, dev)
-
-    # dominant kernel: the fused composite step (one launch per composite step of 18 stages); it is
-    # bound by FP32 arithmetic (the entropic root-find), its global traffic being one read and one
-    # write of the 16 MB state per launch
-    stage_s = statistics.mean(stage_ms) * 1e-3
-    launch_s = stage_s * int(sim.sizes.stages_per_step)
-    flops = FLOPS_PER_CELL_STAGE * N * int(sim.sizes.stages_per_step)
-    achieved = flops / launch_s / 1e12
-    peak, peak_kind = peaks()
-    hbm_bytes = 2 * int(sim.sizes.planes) * N * 4
-    inst_rate = INST_PER_CELL_STAGE * N * int(sim.sizes.stages_per_step) / launch_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": 16.81e6,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "kernel": "k_step1d<ShallowWater<1>, float, entropic> (one composite step per launch)",
-                "launch_us": launch_s * 1e6, "stage_us": stage_s * 1e6,
-                "flops_per_cell_stage": FLOPS_PER_CELL_STAGE,
-                "issue_view": {"inst_per_cell_stage": INST_PER_CELL_STAGE, "achieved_tinst_s": inst_rate,
-                               "peak_tinst_s": ISSUE_PEAK_TINST, "frac": inst_rate / ISSUE_PEAK_TINST,
-                               "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2.07 GHz"},
-                "hbm_view": {"bytes_per_launch": hbm_bytes, "achieved_gbs": hbm_bytes / launch_s / 1e9,
-                             "peak_gbs": peak, "frac": hbm_bytes / launch_s / 1e9 / peak,
-                             "per_stage_model_gbs": 18 * hbm_bytes / launch_s / 1e9,
-                             "peak_source": peak_kind}}
-
+    kern_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    value, _ = aggregate(sum(step_ms), n * n * n_steps * args.steps, dist, dev)
+    bytes_su = 18 * 2 * int(sz.planes) * 4
+    kernel = "k_step2d<Euler2, float, fixed> (temporally blocked, %g launches per step)" % launches_step \
+        if launches_step < 18 else "k_stage_bulk<Euler2, float, fixed> (one launch per stage)"
+    roof = hbm_roofline(bytes_su, n * n * n_steps, statistics.mean(kern_ms) * 1e-3, kernel,
+                        int(round(launches_step * n_steps)),
+                        {"site_updates_per_s_kernel": n * n * n_steps / (statistics.mean(kern_ms) * 1e-3)})
+    with torch.cuda.stream(stream):
+        # conservation over the run (FP64 totals) and the vortex after n steps: finite state
+        t0 = np.asarray(sim.totals())
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     u0_pin = torch.from_numpy(u0_host).pin_memory()
-    u_host = torch.empty((sim.M, N), dtype=torch.float64).pin_memory()
+    u_host = torch.empty((sim.M, n, n), dtype=torch.float64).pin_memory()
     tot_host = np.empty(2 + sim.M)
+    lib = eslbm.lib()
     e2e_times = []
     with torch.cuda.stream(stream):
-        for i in range(args.steps + 1):
+        for i in range(2):
             torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            sim.init_equilibrium(u0_pin.numpy())
+            t = time.perf_counter()
+            sim._check(lib.eslbm_init_equilibrium(sim.h, u0_pin.data_ptr(), 0))
             sim.step(n_steps)
-            lib = eslbm.lib()
             sim._check(lib.eslbm_read_moments(sim.h, u_host.data_ptr(), 0))
             sim._check(lib.eslbm_read_totals(sim.h, tot_host.ctypes.data, 0))
             torch.cuda.synchronize(dev)
             if i:
-                e2e_times.append(time.perf_counter() - t0)
-    e2e_value = world * N * n_steps / statistics.mean(e2e_times)
-    h2d = sim.M * N * 8
-    d2h = sim.M * N * 8 + (2 + sim.M) * 8
-
-    extras = {}
-    if not args.no_extras and rank == 0:
-        extras = fp64_leg(sim, torch, eslbm, inputs, stream, dev, N)
-        extras.update(accuracy_leg(torch, eslbm, inputs, stream, dev))
-        extras.update(adjoint_leg(torch, eslbm, inputs, stream, dev))
-        extras.update(batch_leg(torch, eslbm, inputs, stream, dev))
-        extras.update(hbm2d_leg(torch, eslbm, inputs, stream, dev))
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_extras:
-        rate, dt = oracle_sample(2048)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "1 composite step of the same workload on 2048 cells (FP64 C oracle, %.1f s)" % dt}
-
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "sw1d_d1q2_entropic_n%d_t%g" % (N, args.t_final), "system": "shallow_water",
-                           "lattice": "D1Q2", "N": N, "V": V, "g": G, "t_final": args.t_final,
-                           "composite_steps": n_steps, "stages": stages, "omega": "entropic", "precision": "fp32",
-                           "storage": "shifted, u_ref = (1, 0)",
-                           "cuda_graph": True, "parallelism": "replicas" if world > 1 else "single",
-                           "l2": "flushed between timed steps; the 16 MB state stays L2-resident inside a step"},
-                "roofline": roofline, "cpu_baseline": cpu,
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches_per_step * args.steps, "clocks": clk}
-        line.update(extras)
-        print(json.dumps(line), flush=True)
+                e2e_times.append(time.perf_counter() - t)
+    e2e_value = world * n * n * n_steps / statistics.mean(e2e_times)
     sim.close()
-    if dist:
-        dist.destroy_process_group()
+    launches = 1 + int(round(launches_step * n_steps)) + 1 + 2  # init, steps, gather, totals (two passes)
+    return {"value": value, "ms_per_step": statistics.mean(step_ms), "roofline": roof, "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(sim.M * n * n * 8),
+                    "d2h_bytes_per_step": int(sim.M * n * n * 8 + (2 + sim.M) * 8)},
+            "gpu_launches": launches * args.steps, "mass_total": float(t0[2])}
 
 
-def fp64_leg(sim32, torch, eslbm, inputs, stream, dev, N, nsteps=60):
-    """FP64 composite form and FP64 plain second-order form R T on the same grid: throughput on a
-    bounded number of steps, and the FP32-vs-FP64 L2 difference of h after those steps."""
-    out = {}
+# ---------------------------------------------------------------------------
+# other workloads of the path
+# ---------------------------------------------------------------------------
+
+def timed_steps(torch, sim, stream, dev, n_steps, init=None):
+    """CUDA-event time (ms) of n_steps composite steps from the given initial fields."""
+    with torch.cuda.stream(stream):
+        if init is not None:
+            sim.init_equilibrium(init)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(n_steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1)
+
+
+def sw1d_leg(torch, eslbm, inputs, stream, dev):
+    """1D shallow water, N = 2^20, g = 9.81, V = 4, h0 = 1 + 0.1 sin 2 pi x, at rest, entropic omega,
+    FP32 shifted by the state at rest, to t = 0.05 (8738 composite steps, one temporally blocked launch
+    each): throughput and the per-stage HBM model, with the ALU view of the entropic root-find."""
+    N = SW_N
+    n_steps = inputs.steps_for(SW_T, 1.0 / N, SW_V)
+    cfg = eslbm.make_config(1, "sw", N, V=SW_V, g=G, precision="fp32", omega_mode="entropic", u_ref=SW_UREF)
+    u0 = torch.from_numpy(inputs.sw_sine_1d(N, 1.0, 0.1)).to(dev)
+    with torch.cuda.stream(stream):
+        sim = eslbm.Simulation(cfg, stream=stream, device=dev)
+        sim.use_graph(True)
+        sim.init_equilibrium(u0)
+        sim.step(4)
+    ms = timed_steps(torch, sim, stream, dev, n_steps, init=u0)
+    fb = int(sim.diagnostics()["fallbacks"])
+    planes = int(sim.sizes.planes)
+    sim.close()
+    s = ms * 1e-3
+    flops = SW_FLOPS_PER_CELL_STAGE * N * 18 * n_steps / s / 1e12
+    roof = hbm_roofline(18 * 2 * planes * 4, N * n_steps, s, "k_step1d<ShallowWater<1>, float, entropic>",
+                        n_steps, {"alu_view": {"achieved_tflops": flops, "peak_tflops": FP32_PEAK_TFLOPS,
+                                               "frac": flops / FP32_PEAK_TFLOPS,
+                                               "flops_per_cell_stage": SW_FLOPS_PER_CELL_STAGE}})
+    return {"sw1d": {"workload": "sw1d_d1q2_entropic_n%d_t%g" % (N, SW_T), "N": N, "V": SW_V, "g": G,
+                     "t_final": n_steps * 24.0 / N / SW_V, "composite_steps": n_steps, "ms": ms,
+                     "site_updates_per_s": N * n_steps / s, "roofline": roof, "fallbacks": fb,
+                     "storage": "fp32, shifted, u_ref = (1, 0)", "cuda_graph": True,
+                     "l2": "the 16 MB state is L2-resident within a step"}}
+
+
+def burgers2d_leg(torch, eslbm, inputs, stream, dev):
+    """2D Burgers 4096^2, u0 = 0.5 + 0.25 sin 2 pi x sin 2 pi y + 1e-3 N(0, 1), V = 3, entropic omega,
+    FP32, 2000 composite steps (t = 3.9, past shock formation): throughput, per-stage HBM model,
+    fallbacks, and the total microscopic entropy before and after (it may only decrease)."""
+    n = BURGERS_N
+    cfg = eslbm.make_config(2, "burgers", n, n, V=BURGERS_V, precision="fp32", omega_mode="entropic")
+    u0 = torch.from_numpy(inputs.burgers_2d(n, n)).to(dev)
+    with torch.cuda.stream(stream):
+        sim = eslbm.Simulation(cfg, stream=stream, device=dev)
+        sim.use_graph(True)
+        sim.init_equilibrium(u0)
+        sim.step(2)
+        sim.init_equilibrium(u0)
+        sim.reset_diagnostics()
+        t0 = sim.totals()
+    ms = timed_steps(torch, sim, stream, dev, BURGERS_STEPS)
+    with torch.cuda.stream(stream):
+        t1 = sim.totals()
+        fb = int(sim.diagnostics()["fallbacks"])
+    lps = float(sim.sizes.launches_per_step)
+    sim.close()
+    s = ms * 1e-3
+    kernel = ("k_step2d<Scalar<2, true>, float, entropic> (%g launches per step)" % lps if lps < 18
+              else "k_stage_bulk<Scalar<2, true>, float, entropic>")
+    return {"burgers2d": {"workload": "burgers2d_d2q4_entropic_n%d_steps%d" % (n, BURGERS_STEPS), "V": BURGERS_V,
+                          "t_final": BURGERS_STEPS * 24.0 / n / BURGERS_V, "ms": ms,
+                          "site_updates_per_s": n * n * BURGERS_STEPS / s,
+                          "roofline": hbm_roofline(18 * 2 * 4 * 4, n * n * BURGERS_STEPS, s, kernel,
+                                                   int(round(lps * BURGERS_STEPS))),
+                          "fallbacks": fb, "sigma_total": [float(t0[0]), float(t1[0])],
+                          "mass_total": [float(t0[2]), float(t1[2])]}}
+
+
+def riemann_leg(torch, eslbm, inputs, stream, dev):
+    """Euler 4096^2 seeded random-interface Riemann data (four constant states with rho, p in
+    [0.5, 1.5], u, v in [-0.5, 0.5]), V = 8, scheme III with omega = 2 (the paper's Euler setting),
+    500 composite steps: throughput, and the state checked every 50 steps (finite, min rho, min p)."""
+    n = RIEMANN_N
+    cfg = eslbm.make_config(2, "euler", n, n, V=EULER_V, gamma=EULER_GAMMA, precision="fp32", omega_mode="fixed",
+                            scheme="III")
+    u0 = torch.from_numpy(inputs.euler_riemann_2d(n, n)).to(dev)
+    with torch.cuda.stream(stream):
+        sim = eslbm.Simulation(cfg, stream=stream, device=dev)
+        sim.use_graph(True)
+        sim.init_equilibrium(u0)
+        sim.step(2)
+    ms = timed_steps(torch, sim, stream, dev, RIEMANN_STEPS, init=u0)
+    rows = []
+    with torch.cuda.stream(stream):
+        sim.init_equilibrium(u0)
+        for k in range(RIEMANN_STEPS // 50):
+            sim.step(50)
+            u = sim.moments()
+            rho = u[0]
+            p = (EULER_GAMMA - 1) * (u[3] - 0.5 * (u[1] ** 2 + u[2] ** 2) / rho)
+            fin = bool(torch.isfinite(u).all())
+            rows.append({"steps": 50 * (k + 1), "finite": fin, "rho_min": float(rho.min()), "p_min": float(p.min())})
+            if not fin:
+                break
+    lps = float(sim.sizes.launches_per_step)
+    sim.close()
+    s = ms * 1e-3
+    return {"euler_riemann": {"workload": "euler2d_d2q4_riemann_n%d_steps%d_schemeIII" % (n, RIEMANN_STEPS),
+                              "ms": ms, "site_updates_per_s": n * n * RIEMANN_STEPS / s,
+                              "roofline": hbm_roofline(27 * 2 * 16 * 4, n * n * RIEMANN_STEPS, s,
+                                                       "k_step2d<Euler2, float, fixed>", int(round(lps * RIEMANN_STEPS)),
+                                                       {"model": "per-stage: 27 x 2 q M b bytes per step (scheme III)"}),
+                              "state": rows}}
+
+
+def precision_leg(torch, eslbm, inputs, stream, dev, N=1 << 18):
+    """The precision split on the 1D shallow-water workload to t = 0.05: FP32 storage with the
+    entropic omega in FP32, FP32 storage with the entropy difference in FP64 (mixed), against the
+    all-FP64 path on the same grid: relative L2 error of the state at the final time and time per
+    composite step, plus the per-cell entropy check (diagnostics) of each mode."""
+    n_steps = inputs.steps_for(SW_T, 1.0 / N, SW_V)
     u0 = torch.from_numpy(inputs.sw_sine_1d(N, 1.0, 0.1)).to(dev)
     res = {}
+    for name, prec, uref in (("fp64", "fp64", None), ("fp32", "fp32", None), ("fp32_shifted", "fp32", SW_UREF),
+                             ("fp32_mixed_shifted", "fp32_mixed", SW_UREF)):
+        cfg = eslbm.make_config(1, "sw", N, V=SW_V, g=G, precision=prec, omega_mode="entropic", u_ref=uref)
+        with torch.cuda.stream(stream):
+            sim = eslbm.Simulation(cfg, stream=stream, device=dev)
+            sim.use_graph(True)
+            sim.init_equilibrium(u0)
+            sim.step(2)
+        ms = timed_steps(torch, sim, stream, dev, n_steps, init=u0)
+        with torch.cuda.stream(stream):
+            u = sim.moments().cpu().numpy()
+        sim.close()
+        # the per-cell check over the first 64 steps, in the same kernels
+        cfg_d = eslbm.make_config(1, "sw", N, V=SW_V, g=G, precision=prec, omega_mode="entropic", u_ref=uref,
+                                  diagnostics=True)
+        with torch.cuda.stream(stream):
+            simd = eslbm.Simulation(cfg_d, stream=stream, device=dev)
+            simd.init_equilibrium(u0)
+            simd.step(64)
+            d = simd.diagnostics()
+            simd.close()
+        res[name] = {"u": u, "ms_per_step": ms / n_steps, "entropy_increases_64_steps": int(d["entropy_increases"]),
+                     "entropy_excess_max": float(d["entropy_excess_max"])}
+    ref = res["fp64"]["u"]
+    out = {}
+    for name, r in res.items():
+        row = {"ms_per_composite_step": r["ms_per_step"], "entropy_increases_64_steps": r["entropy_increases_64_steps"],
+               "entropy_excess_max": r["entropy_excess_max"]}
+        if name != "fp64":
+            a = r["u"]
+            row["rel_l2_h"] = float(np.linalg.norm(a[0] - ref[0]) / np.linalg.norm(ref[0]))
+            row["rel_l2_hu"] = float(np.linalg.norm(a[1] - ref[1]) / max(np.linalg.norm(ref[1]), 1e-300))
+            row["rel_l2_state"] = float(np.linalg.norm(a - ref) / np.linalg.norm(ref))
+        out[name] = row
+    return {"precision": {"workload": "sw1d entropic, N = %d, t = %.4f (%d composite steps)"
+                                      % (N, n_steps * 24.0 / N / SW_V, n_steps),
+                          "reference": "fp64 composite on the same grid", "modes": out}}
+
+
+def fp32_vs_fp64_leg(torch, eslbm, inputs, stream, dev, N=SW_N, nsteps=60):
+    """FP64 composite form and FP64 plain second-order form R T on the 1D shallow-water grid:
+    throughput on a bounded number of steps."""
+    out = {}
+    u0 = torch.from_numpy(inputs.sw_sine_1d(N, 1.0, 0.1)).to(dev)
     for name, prec, scheme, steps in (("fp64_composite", "fp64", "I", nsteps), ("fp32_composite", "fp32", "I", nsteps),
                                       ("fp64_plain", "fp64", "plain", 24 * nsteps)):
-        cfg = eslbm.make_config(1, "sw", N, V=V, g=G, precision=prec, omega_mode="entropic" if scheme == "I" else "fixed",
-                                scheme=scheme, u_ref=U_REF if prec == "fp32" else None)
+        cfg = eslbm.make_config(1, "sw", N, V=SW_V, g=G, precision=prec,
+                                omega_mode="entropic" if scheme == "I" else "fixed", scheme=scheme,
+                                u_ref=SW_UREF if prec == "fp32" else None)
         with torch.cuda.stream(stream):
             sim = eslbm.Simulation(cfg, stream=stream, device=dev)
             sim.use_graph(True)
             sim.init_equilibrium(u0)
             sim.step(2 if scheme == "I" else 48)
-            torch.cuda.synchronize(dev)
-            sim.init_equilibrium(u0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sim.step(steps)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            ms = e0.elapsed_time(e1)
-            res[name] = sim.moments().cpu().numpy()
-            sim.close()
+        ms = timed_steps(torch, sim, stream, dev, steps, init=u0)
+        sim.close()
         site_steps = N * (steps if scheme == "I" else steps / 24.0)
-        out[name] = {"site_updates_per_s": site_steps / (ms * 1e-3), "ms": ms,
-                     "steps": steps, "scheme": scheme, "omega": "entropic" if scheme == "I" else "fixed 2"}
-    ref = res["fp64_composite"][0]
-    nrm = np.linalg.norm(ref)
-    out["fp32_composite"]["rel_l2_h_vs_fp64"] = float(np.linalg.norm(res["fp32_composite"][0] - ref) / nrm)
-    out["fp64_plain"]["rel_l2_h_vs_fp64_composite"] = float(np.linalg.norm(res["fp64_plain"][0] - ref) / nrm)
-    return {"fp32_vs_fp64": {"N": N, "t": nsteps * 24.0 / N / V, **out}}
-
-
-def fp32err_leg(torch, eslbm, inputs, stream, dev, N=N_CELLS, t_final=T_FINAL):
-    """Error of the FP32 composite solution against the FP64 composite solution of the bench workload
-    (1D shallow water, entropic omega) at the final time, relative L2 of h and of hu, with the error after
-    1/8, 1/4, 1/2 of the steps (rounding accumulates with the number of stages).  FP64 runs at 1/64 of
-    the FP32 rate on this GPU, so the full-size case takes minutes."""
-    n_steps = inputs.steps_for(t_final, 1.0 / N, V)
-    marks = sorted(set([max(1, n_steps // 8), max(1, n_steps // 4), max(1, n_steps // 2), n_steps]))
-    u0 = torch.from_numpy(inputs.sw_sine_1d(N, 1.0, 0.1)).to(dev)
-    res = {}
-    for prec in ("fp32", "fp32_shifted", "fp64"):
-        cfg = eslbm.make_config(1, "sw", N, V=V, g=G, precision=prec[:4], omega_mode="entropic",
-                                u_ref=U_REF if prec == "fp32_shifted" else None)
-        with torch.cuda.stream(stream):
-            sim = eslbm.Simulation(cfg, stream=stream, device=dev)
-            sim.use_graph(True)
-            sim.init_equilibrium(u0)
-            done, out = 0, []
-            for mk in marks:
-                sim.step(mk - done)
-                done = mk
-                out.append(sim.moments().cpu().numpy())
-            res[prec] = out
-            sim.close()
-    rows = []
-    for i, mk in enumerate(marks):
-        b = res["fp64"][i]
-        row = {"steps": mk, "t": mk * 24.0 / N / V}
-        for name in ("fp32", "fp32_shifted"):
-            a = res[name][i]
-            row[name] = {"rel_l2_h": float(np.linalg.norm(a[0] - b[0]) / np.linalg.norm(b[0])),
-                         "rel_l2_hu": float(np.linalg.norm(a[1] - b[1]) / max(np.linalg.norm(b[1]), 1e-300)),
-                         "rel_l2_state": float(np.linalg.norm(a - b) / np.linalg.norm(b))}
-        rows.append(row)
-    return {"fp32_error": {"N": N, "t_final": t_final, "reference": "fp64 composite (same scheme, same grid)",
-                           "rows": rows}}
+        out[name] = {"site_updates_per_s": site_steps / (ms * 1e-3), "ms": ms, "steps": steps, "scheme": scheme,
+                     "omega": "entropic" if scheme == "I" else "fixed 2"}
+    return {"fp32_vs_fp64": {"N": N, **out}}
 
 
 def accuracy_leg(torch, eslbm, inputs, stream, dev, n_ref=1 << 16, sizes=tuple(1 << k for k in range(8, 17)),
@@ -421,26 +503,21 @@ def accuracy_leg(torch, eslbm, inputs, stream, dev, n_ref=1 << 16, sizes=tuple(1
     error is the relative discrete L2 norm of h against the FP64 composite solution on 2^16 cells, sampled
     at the coarse points (cells at j dx on every grid).  Times are CUDA-event times of the steps alone."""
     def run(N, prec, scheme, n_comp):
-        cfg = eslbm.make_config(1, "sw", N, V=V, g=G, precision=prec,
+        cfg = eslbm.make_config(1, "sw", N, V=SW_V, g=G, precision=prec,
                                 omega_mode="entropic" if scheme == "I" else "fixed", omega=2.0, scheme=scheme,
-                                u_ref=U_REF if prec == "fp32" else None)
+                                u_ref=SW_UREF if prec == "fp32" else None)
         steps = n_comp if scheme == "I" else 24 * n_comp
+        u0 = torch.from_numpy(inputs.sw_sine_1d(N, 1.0, 0.1)).to(dev)
         with torch.cuda.stream(stream):
             sim = eslbm.Simulation(cfg, stream=stream, device=dev)
             sim.use_graph(True)
-            u0 = torch.from_numpy(inputs.sw_sine_1d(N, 1.0, 0.1)).to(dev)
             sim.init_equilibrium(u0)
             sim.step(1)  # warm-up and graph capture
-            sim.init_equilibrium(u0)
-            torch.cuda.synchronize(dev)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sim.step(steps)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
+        ms = timed_steps(torch, sim, stream, dev, steps, init=u0)
+        with torch.cuda.stream(stream):
             h = sim.moments().cpu().numpy()[0]
-            sim.close()
-        return h, e0.elapsed_time(e1)
+        sim.close()
+        return h, ms
 
     n_at = lambda N: 2 * N // 256  # composite steps to t = 0.046875
     ref, _ = run(n_ref, "fp64", "I", n_at(n_ref))
@@ -462,15 +539,15 @@ def accuracy_leg(torch, eslbm, inputs, stream, dev, n_ref=1 << 16, sizes=tuple(1
         if pick["fp32_composite"] and pick["fp64_plain"]:
             pick["speedup_fp32_composite"] = pick["fp64_plain"]["ms"] / pick["fp32_composite"]["ms"]
         best["%g" % eps] = pick
-    return {"time_to_accuracy": {"t": 2 * 24 / (256 * V), "reference": "fp64 composite, N = %d" % n_ref,
+    return {"time_to_accuracy": {"t": 2 * 24 / (256 * SW_V), "reference": "fp64 composite, N = %d" % n_ref,
                                  "sweep": rows, "at_target_rel_l2": best}}
 
 
 def adjoint_leg(torch, eslbm, inputs, stream, dev, N=1 << 16, n=96, K=16):
-    """Reverse mode against forward on the same workload shape (1D shallow water, FP32, entropic):
-    one forward solve (init, n steps, moments) and one eslbm_gradient (forward with checkpoints
-    every K steps, segment and step recomputation, adjoint stages)."""
-    cfg = eslbm.make_config(1, "sw", N, V=V, g=G, precision="fp32", omega_mode="entropic")
+    """Reverse mode against forward on the 1D shallow-water workload shape (FP32, entropic): one forward
+    solve (init, n steps, moments) and one eslbm_gradient (forward with checkpoints every K steps,
+    segment and step recomputation, adjoint stages)."""
+    cfg = eslbm.make_config(1, "sw", N, V=SW_V, g=G, precision="fp32", omega_mode="entropic")
     with torch.cuda.stream(stream):
         sim = eslbm.Simulation(cfg, stream=stream, device=dev)
         u0 = torch.from_numpy(inputs.sw_sine_1d(N, 1.0, 0.1)).to(dev)
@@ -492,14 +569,14 @@ def adjoint_leg(torch, eslbm, inputs, stream, dev, N=1 << 16, n=96, K=16):
                                    "adjoint_s": times["adjoint"], "ratio": times["adjoint"] / times["forward"]}}
 
 
-def batch_leg(torch, eslbm, inputs, stream, dev, count=64, steps=20, grad_instances=4, grad_n=50, grad_K=10):
-    """Batched form: `count` 2D shallow-water instances (D2Q4, FP32, entropic) of uneven seeded sizes in
-    [256, 1024]^2 with 8-mode Fourier depth data, advanced by one cooperative launch per composite step
-    replayed from CUDA graphs, after the autotuner has picked the schedule; a bounded number of steps.
-    The reverse mode is timed on the first `grad_instances` instances (L2 misfit of the final depth
-    against a seeded target, checkpoints every grad_K steps).  FP32 storage shifted by the state at rest
-    of depth 1; its error after the timed steps is stated against FP64 single-lattice runs of two
-    instances."""
+def batch_leg(torch, eslbm, inputs, stream, dev, count=64, steps=BATCH_STEPS, K=BATCH_K, grad=True):
+    """Batched form: `count` 2D shallow-water instances (D2Q4, FP32 shifted by the state at rest of depth
+    1, entropic) of uneven seeded sizes in [256, 1024]^2 with 8-mode Fourier depth data, advanced by one
+    cooperative launch per composite step replayed from CUDA graphs, after the autotuner has picked the
+    schedule, for `steps` composite steps; then the reverse mode: the gradient of the L2 misfit of the
+    final depth against a seeded target with respect to the initial depth of every instance,
+    checkpoints every K steps.  The FP32 error after the steps is stated against FP64 single-lattice
+    runs of two instances."""
     sizes = inputs.batched_sizes(count, 256, 1024)
     cfg = eslbm.make_config(2, "sw", 1, 1, V=BATCH_V, g=G, precision="fp32", omega_mode="entropic",
                             u_ref=(1.0, 0.0, 0.0))
@@ -512,7 +589,7 @@ def batch_leg(torch, eslbm, inputs, stream, dev, count=64, steps=20, grad_instan
         tune_s = time.perf_counter() - t0
         b.use_graph(True)
         b.init_equilibrium(u0)
-        b.step(steps)  # warm-up: captures the graphs
+        b.step(2)  # warm-up: captures the graphs
         b.init_equilibrium(u0)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -529,88 +606,122 @@ def batch_leg(torch, eslbm, inputs, stream, dev, count=64, steps=20, grad_instan
             nx, ny = sizes[i]
             c64 = eslbm.make_config(2, "sw", nx, ny, V=BATCH_V, g=G, precision="fp64", omega_mode="entropic")
             s64 = eslbm.Simulation(c64, stream=stream, device=dev)
+            s64.use_graph(True)
             s64.init_equilibrium(torch.from_numpy(inputs.sw_fourier_2d(nx, ny, seed=1000 + i)).to(dev))
             s64.step(steps)
             ref = s64.moments()
             s64.close()
             errs.append(float(torch.linalg.vector_norm(fp32[i][0] - ref[0]) / torch.linalg.vector_norm(ref[0])))
+        out = {"instances": count, "total_cells": cells, "sizes": "seeded uniform nx, ny in [256, 1024]",
+               "steps": steps, "ms": ms, "site_updates_per_s": cells * steps / (ms * 1e-3),
+               "roofline": hbm_roofline(18 * 2 * 12 * 4, cells * steps, ms * 1e-3,
+                                        "k_batch_step<ShallowWater<2>, float, entropic>", steps),
+               "schedule": {"segment": sched[0], "blocks_per_sm": sched[1], "order": sched[2]},
+               "tune_s": tune_s, "cuda_graph": True, "fallbacks": fallbacks, "V": BATCH_V,
+               "storage": "fp32, shifted, u_ref = (1, 0, 0)",
+               "rel_l2_h_vs_fp64": {"instances": [list(sizes[0]), list(sizes[1])], "values": errs}}
+        if grad:
+            target = b.pack([inputs.sw_fourier_2d(nx, ny, seed=5000 + i) for i, (nx, ny) in enumerate(sizes)])
+            torch.cuda.synchronize(dev)
+            tf = time.perf_counter()
+            b.init_equilibrium(u0)
+            b.step(steps)
+            uT = b.moments_flat()
+            torch.cuda.synchronize(dev)
+            fwd_s = time.perf_counter() - tf
+            lam = torch.zeros_like(uT)
+            for v, (u, t) in enumerate(zip(b.unpack(uT), b.unpack(target))):
+                b.unpack(lam)[v][0] = 2.0 * (u[0] - t[0])  # dJ/dh_T of J = sum (h_T - target)^2
+            torch.cuda.synchronize(dev)
+            ta = time.perf_counter()
+            g = b.gradient(u0, lam, steps, K)
+            torch.cuda.synchronize(dev)
+            adj_s = time.perf_counter() - ta
+            out["adjoint"] = {"instances": count, "steps": steps, "checkpoint_every": K, "forward_s": fwd_s,
+                              "gradient_s": adj_s, "ratio": adj_s / fwd_s, "grad_norm": float(torch.linalg.vector_norm(g)),
+                              "finite": bool(torch.isfinite(g).all())}
         b.close()
-        # reverse mode on a bounded sample of the instances
-        gs = sizes[:grad_instances]
-        gb = eslbm.Batch(cfg, gs, stream=stream, device=dev)
-        gu0 = gb.pack([inputs.sw_fourier_2d(nx, ny, seed=1000 + i) for i, (nx, ny) in enumerate(gs)])
-        target = gb.pack([inputs.sw_fourier_2d(nx, ny, seed=5000 + i) for i, (nx, ny) in enumerate(gs)])
-        torch.cuda.synchronize(dev)
-        tf = time.perf_counter()
-        gb.init_equilibrium(gu0)
-        gb.step(grad_n)
-        uT = gb.moments_flat()
-        torch.cuda.synchronize(dev)
-        fwd_s = time.perf_counter() - tf
-        lam = torch.zeros_like(uT)
-        for v, (u, t) in enumerate(zip(gb.unpack(uT), gb.unpack(target))):
-            gb.unpack(lam)[v][0] = 2.0 * (u[0] - t[0])  # dJ/dh_T of J = sum (h_T - target)^2
-        torch.cuda.synchronize(dev)
-        ta = time.perf_counter()
-        grad = gb.gradient(gu0, lam, grad_n, grad_K)
-        torch.cuda.synchronize(dev)
-        adj_s = time.perf_counter() - ta
-        gnorm = float(torch.linalg.vector_norm(grad))
-        gb.close()
-    return {"batched": {"instances": count, "total_cells": cells, "sizes": "seeded uniform nx, ny in [256, 1024]",
-                        "steps": steps, "ms": ms, "site_updates_per_s": cells * steps / (ms * 1e-3),
-                        "schedule": {"segment": sched[0], "blocks_per_sm": sched[1], "order": sched[2]},
-                        "tune_s": tune_s, "cuda_graph": True, "fallbacks": fallbacks, "V": BATCH_V,
-                        "storage": "fp32, shifted, u_ref = (1, 0, 0)",
-                        "rel_l2_h_vs_fp64": {"instances": [list(sizes[0]), list(sizes[1])], "values": errs},
-                        "adjoint": {"instances": grad_instances, "steps": grad_n, "checkpoint_every": grad_K,
-                                    "forward_s": fwd_s, "gradient_s": adj_s, "ratio": adj_s / fwd_s,
-                                    "grad_norm": gnorm}}}
+    return {"batched": out}
 
 
-def hbm2d_leg(torch, eslbm, inputs, stream, dev, steps=20, only=None):
-    """Per-stage streaming rate of the 2D stage kernel (one fused pull-shift + relax launch per stage,
-    every distribution read and written once): D2Q4 Burgers 4096^2 FP32 (32 B per cell-stage) with
-    omega = 2 and with the entropic omega, and D2Q4 Euler 8192^2 FP32 (128 B per cell-stage) with
-    omega = 2 and scheme III (the paper's Euler setting).  Inputs are larger than L2 (268 MB and
-    4.3 GB per state buffer), so every stage streams from HBM."""
-    peak, kind = peaks()
-    cases = [("burgers2d_4096_fixed", 2, "burgers", 4096, dict(V=3.0, c=(1.0, 1.0)), "fixed", "I", steps,
-              lambda n: inputs.burgers_2d(n, n)),
-             ("burgers2d_4096_entropic", 2, "burgers", 4096, dict(V=3.0, c=(1.0, 1.0)), "entropic", "I", steps,
-              lambda n: inputs.burgers_2d(n, n)),
-             ("euler2d_8192_fixed", 2, "euler", 8192, dict(V=8.0, gamma=1.4), "fixed", "III", max(1, steps // 10),
-              lambda n: inputs.euler_vortex_2d(n, n))]
+def cpu_leg():
+    """The FP64 oracle on the host cores: single-threaded and OpenMP over every core, on bounded samples
+    of the headline and of the 1D workload (rates in site updates per second)."""
     out = {}
-    for name, dim, system, n, kw, mode, scheme, nsteps, init in cases:
-        if only and name != only:
-            continue
-        cfg = eslbm.make_config(dim, system, n, n, precision="fp32", omega_mode=mode, scheme=scheme, **kw)
-        with torch.cuda.stream(stream):
-            sim = eslbm.Simulation(cfg, stream=stream, device=dev)
-            sim.use_graph(True)
-            u0 = torch.from_numpy(init(n)).to(dev)
-            sim.init_equilibrium(u0)
-            del u0
-            sim.step(1)  # warm-up and graph capture
-            torch.cuda.synchronize(dev)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sim.step(nsteps)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            ms = e0.elapsed_time(e1)
-            stages = nsteps * int(sim.sizes.stages_per_step)
-            bytes_stage = 2 * int(sim.sizes.state_bytes)
-            fb = int(sim.diagnostics()["fallbacks"])
-            sim.close()
-        stage_s = ms * 1e-3 / stages
-        out[name] = {"cells": n * n, "steps": nsteps, "stages": stages, "stage_us": stage_s * 1e6,
-                     "bytes_per_stage": bytes_stage, "achieved_gbs": bytes_stage / stage_s / 1e9,
-                     "frac_of_hbm_peak": bytes_stage / stage_s / 1e9 / peak, "peak_gbs": peak, "peak_source": kind,
-                     "site_updates_per_s": n * n * nsteps / (ms * 1e-3), "fallbacks": fb,
-                     "kernel": "%s<%s, 2, float, %s>" % ("k_stage_bulk" if n % 4 == 0 else "k_stage", system, mode)}
-    return {"hbm2d": out}
+    for wl in ("euler", "sw1d"):
+        for omp in (False, True):
+            r, dt, desc, threads = oracle_rate(wl, omp)
+            out["%s_%s" % (wl, "openmp" if omp else "single")] = {"site_updates_per_s": r, "seconds": dt,
+                                                                   "threads": threads, "sample": desc}
+    return {"cpu_oracle": out}
+
+
+# ---------------------------------------------------------------------------
+# main
+# ---------------------------------------------------------------------------
+
+LEGS = {"sw1d": sw1d_leg, "burgers2d": burgers2d_leg, "riemann": riemann_leg, "batched": batch_leg,
+        "precision": precision_leg, "accuracy": accuracy_leg, "adjoint": adjoint_leg}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    if args.leg == "cpu":
+        print(json.dumps(cpu_leg()), flush=True)
+        return
+    import torch
+    from paper_2403_13406_gb300 import eslbm, inputs
+    if args.leg:
+        torch.cuda.set_device(0)
+        dev = torch.device("cuda", 0)
+        stream = torch.cuda.Stream(device=dev)
+        kw = {"count": args.batch_count} if args.leg == "batched" else {}
+        print(json.dumps(LEGS[args.leg](torch, eslbm, inputs, stream, dev, **kw)), flush=True)
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", local if world > 1 else 0)
+    stream = torch.cuda.Stream(device=dev)
+
+    head = headline(torch, eslbm, inputs, stream, dev, args, world, dist, local)
+    extras, cpu = {}, None
+    if not args.no_extras and rank == 0:
+        for leg in (sw1d_leg, burgers2d_leg, riemann_leg, precision_leg, fp32_vs_fp64_leg, accuracy_leg,
+                    adjoint_leg):
+            extras.update(leg(torch, eslbm, inputs, stream, dev))
+        extras.update(batch_leg(torch, eslbm, inputs, stream, dev, count=args.batch_count))
+    if rank == 0 and world == 1 and not args.no_extras:
+        c = cpu_leg()["cpu_oracle"]
+        extras["cpu_oracle"] = c
+        e = c["euler_single"]
+        cpu = {"value": e["site_updates_per_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "FP64 C oracle, single thread: %s, %.1f s" % (e["sample"], e["seconds"]),
+               "openmp": {"value": c["euler_openmp"]["site_updates_per_s"], "cores": c["euler_openmp"]["threads"],
+                          "sample": c["euler_openmp"]["sample"]}}
+    if rank == 0:
+        line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(headline_config(args.n, args.composite_steps),
+                               parallelism="replicas" if world > 1 else "single", cuda_graph=True),
+                "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": head["e2e"],
+                "gpu_launches": head["gpu_launches"], "clocks": head["clocks"]}
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

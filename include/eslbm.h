@@ -70,10 +70,13 @@ enum { ESLBM_LINEAR = 0, ESLBM_BURGERS = 1, ESLBM_SHALLOW_WATER = 2, ESLBM_EULER
    (0, -E0) and (t, F(t)), which never exceeds the root of the convex F, replaces
    t.  With a fixed omega FP32_MIXED is FP32. */
 enum { ESLBM_FP32 = 0, ESLBM_FP64 = 1, ESLBM_FP32_MIXED = 2 };
-/* Temporal blocking: AUTO runs several fused stages per launch from on-chip
-   memory where a kernel for it exists (1D: every step); OFF runs one launch per
-   fused stage (the same per-cell arithmetic; used to cross-check the blocked
-   kernels). */
+/* Temporal blocking (eslbm_config.blocking): AUTO runs several fused stages per
+   launch from on-chip memory where a kernel for it exists -- 1D: every step in
+   one launch; 2D with rows on 16-byte boundaries (nx a multiple of 4 in FP32 and
+   FP32_MIXED, of 2 in FP64): the stages of a step in a few launches of up to a
+   default number of stages.  OFF runs one launch per fused stage (the same
+   per-cell arithmetic; used to cross-check the blocked kernels).  A value n in
+   [2, 32] is AUTO with at most n stages per 2D launch. */
 enum { ESLBM_BLOCKING_AUTO = 0, ESLBM_BLOCKING_OFF = 1 };
 enum { ESLBM_OMEGA_FIXED = 0, ESLBM_OMEGA_ENTROPIC = 1 };
 /* Schemes (I)-(IV) of Section 6.1; PLAIN is the standard scheme R T(kappa dx/V)
@@ -104,7 +107,7 @@ typedef struct {
                            (eslbm_diagnostics); the same kernels run, the results do not change */
     int32_t shifted;    /* 1: store g = f - fbar with fbar_k = f^eq_k(u_ref) (see below); 0: store f */
     double u_ref[4];    /* reference conserved state of the shifted storage (M values used) */
-    int32_t blocking;   /* ESLBM_BLOCKING_AUTO or ESLBM_BLOCKING_OFF */
+    int32_t blocking;   /* ESLBM_BLOCKING_AUTO, ESLBM_BLOCKING_OFF, or 2..32 (see above) */
     int32_t reserved;   /* 0 */
 } eslbm_config;
 
@@ -130,6 +133,10 @@ typedef struct {
     uint64_t workspace_bytes;/* bytes of the workspace */
     int64_t stages_per_step; /* fused relax-plus-shift stages per step of the scheme */
     int64_t step_cells;      /* lattice time of one step in units of dx / V (24 kappa for I-IV) */
+    double launches_per_step;/* relaxation kernel launches per step in steady state (1D: one per
+                                step, or one per 24 steps of the short schemes; 2D blocked: one per
+                                group of stages; otherwise one per stage); diagnostics add one
+                                check launch after each */
 } eslbm_sizes;
 
 /* Per-cell entropy check (diagnostics = 1, entropic omega, Section 4): for every

@@ -42,14 +42,27 @@ class Stats(ctypes.Structure):
                 "omega_min": self.omega_min, "omega_max": self.omega_max}
 
 
-_lib = None
+_libs = {}
+_openmp = False
 _D = ctypes.POINTER(ctypes.c_double)
 
 
+def set_openmp(enable):
+    """Route later calls to the OpenMP build (cells and planes split over the host cores, the same
+    per-cell arithmetic) or back to the single-threaded one.  Returns False, and stays
+    single-threaded, where the compiler has no OpenMP."""
+    global _openmp
+    if enable and _build.build_openmp() is None:
+        _openmp = False
+        return False
+    _openmp = bool(enable)
+    return True
+
+
 def lib():
-    global _lib
-    if _lib is None:
-        L = ctypes.CDLL(_build.build())
+    key = "omp" if _openmp else "single"
+    if key not in _libs:
+        L = ctypes.CDLL(_build.build_openmp() if _openmp else _build.build())
         P = ctypes.POINTER(_Model)
         S = ctypes.POINTER(Stats)
         sig = {
@@ -77,8 +90,8 @@ def lib():
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
-        _lib = L
-    return _lib
+        _libs[key] = L
+    return _libs[key]
 
 
 def _ptr(a):

@@ -11,26 +11,44 @@ SRC = os.path.join(HERE, "eslbm_oracle.c")
 HDR = os.path.join(HERE, "eslbm_oracle.h")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
+LIB_OMP = os.path.join(OUT_DIR, "liboracle_omp.so")  # the same source with OpenMP over cells and planes
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return t >= os.path.getmtime(SRC) and t >= os.path.getmtime(HDR)
 
 
-def build(force: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
+def _compile(lib, extra):
     os.makedirs(OUT_DIR, exist_ok=True)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-Wall", "-Wextra", "-o", tmp, SRC, "-lm"]
+           "-shared", "-Wall", "-Wextra", "-Wno-unknown-pragmas", *extra, "-o", tmp, SRC, "-lm"]
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build(force: bool = False) -> str:
+    """The single-threaded oracle (what the tests load)."""
+    if not force and up_to_date(LIB):
+        return LIB
+    return _compile(LIB, [])
+
+
+def build_openmp(force: bool = False):
+    """The OpenMP build (cells and planes split over the host cores; the same arithmetic per cell),
+    or None where the compiler has no OpenMP."""
+    if not force and up_to_date(LIB_OMP):
+        return LIB_OMP
+    try:
+        return _compile(LIB_OMP, ["-fopenmp"])
+    except (subprocess.CalledProcessError, OSError):
+        return None
 
 
 if __name__ == "__main__":
     print(build(force=True))
+    print(build_openmp(force=True))

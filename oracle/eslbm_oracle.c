@@ -571,40 +571,74 @@ int or_transport(const or_model *m, double *f, long s)
 {
     int q = or_q(m), M = or_M(m);
     long n = or_ncell(m);
-    double *tmp = (double *)malloc(sizeof(double) * (size_t)n);
-    if (!tmp) return -1;
     long reps = s < 0 ? -s : s;
     int dir_t = s < 0 ? -1 : 1;
-    for (long r = 0; r < reps; ++r)
-        for (int k = 0; k < q; ++k)
-            for (int i = 0; i < M; ++i)
-                unit_shift_plane(m, f + (long)(k * M + i) * n, vel_axis(m, k),
-                                 dir_t * vel_sign(m, k), tmp);
-    free(tmp);
-    return 0;
+    int err = 0;
+    /* the planes are independent: with OpenMP each thread shifts whole planes */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(| : err)
+#endif
+    for (int l = 0; l < q * M; ++l) {
+        double *tmp = (double *)malloc(sizeof(double) * (size_t)n);
+        if (!tmp) {
+            err = 1;
+            continue;
+        }
+        int k = l / M;
+        for (long r = 0; r < reps; ++r)
+            unit_shift_plane(m, f + (long)l * n, vel_axis(m, k), dir_t * vel_sign(m, k), tmp);
+        free(tmp);
+    }
+    return err ? -1 : 0;
 }
 
-/* f_k <- (1 - omega) f_k + omega f^eq_k(u)  (eq. relaxationDiscretizationOmega) */
+static void merge_stats(or_stats *into, const or_stats *from)
+{
+    into->relaxations += from->relaxations;
+    into->fallbacks += from->fallbacks;
+    if (from->omega_min < into->omega_min) into->omega_min = from->omega_min;
+    if (from->omega_max > into->omega_max) into->omega_max = from->omega_max;
+}
+
+/* f_k <- (1 - omega) f_k + omega f^eq_k(u)  (eq. relaxationDiscretizationOmega).
+   Cells are independent: with OpenMP each thread relaxes a block of cells with the
+   same arithmetic and keeps its own statistics, merged at the end. */
 int or_relax(const or_model *m, double *f, int kind, or_stats *st)
 {
     int q = or_q(m), M = or_M(m);
     long n = or_ncell(m);
-    double fc[16], u[4], feq[16];
-    for (long x = 0; x < n; ++x) {
-        for (int l = 0; l < q * M; ++l) fc[l] = f[(long)l * n + x];
-        double w;
-        if (kind == OR_R_PROJECT) {
-            w = 1.0;
-        } else {
-            w = or_omega(m, fc, st);
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+    {
+        or_stats local = {0, 0, INFINITY, -INFINITY};
+        or_stats *ls = st ? &local : NULL;
+        double fc[16], u[4], feq[16];
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+        for (long x = 0; x < n; ++x) {
+            for (int l = 0; l < q * M; ++l) fc[l] = f[(long)l * n + x];
+            double w;
+            if (kind == OR_R_PROJECT) {
+                w = 1.0;
+            } else {
+                w = or_omega(m, fc, ls);
+            }
+            for (int i = 0; i < M; ++i) {
+                double s = 0.0;
+                for (int k = 0; k < q; ++k) s += fc[k * M + i];
+                u[i] = s;
+            }
+            or_equilibrium(m, u, feq);
+            for (int l = 0; l < q * M; ++l) f[(long)l * n + x] = (1.0 - w) * fc[l] + w * feq[l];
         }
-        for (int i = 0; i < M; ++i) {
-            double s = 0.0;
-            for (int k = 0; k < q; ++k) s += fc[k * M + i];
-            u[i] = s;
+        if (st) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+            merge_stats(st, &local);
         }
-        or_equilibrium(m, u, feq);
-        for (int l = 0; l < q * M; ++l) f[(long)l * n + x] = (1.0 - w) * fc[l] + w * feq[l];
     }
     return 0;
 }

@@ -32,7 +32,7 @@ eslbm_status validate(const eslbm_config *c)
     if (c->system < ESLBM_LINEAR || c->system > ESLBM_EULER) return ESLBM_ERR_ARG;
     if (c->precision != ESLBM_FP32 && c->precision != ESLBM_FP64 && c->precision != ESLBM_FP32_MIXED)
         return ESLBM_ERR_ARG;
-    if (c->blocking != ESLBM_BLOCKING_AUTO && c->blocking != ESLBM_BLOCKING_OFF) return ESLBM_ERR_ARG;
+    if (c->blocking < 0 || c->blocking > kStep2dMaxStages) return ESLBM_ERR_ARG;
     if (c->omega_mode != ESLBM_OMEGA_FIXED && c->omega_mode != ESLBM_OMEGA_ENTROPIC) return ESLBM_ERR_ARG;
     if (c->scheme < ESLBM_SCHEME_I || c->scheme > ESLBM_SCHEME_B) return ESLBM_ERR_ARG;
     if (c->kappa < 1 || c->kappa > 1024) return ESLBM_ERR_ARG;
@@ -56,6 +56,34 @@ eslbm_status validate(const eslbm_config *c)
     }
     return ESLBM_OK;
 }
+
+// steps fused into one launch of the 1D kernel: one composite step, or up to 24 steps of the
+// short schemes
+int64_t fused_group_of(int64_t stages_per_step)
+{
+    return stages_per_step >= 16 ? 1 : std::max<int64_t>(1, 24 / stages_per_step);
+}
+
+// most stages of one launch of the 2D kernel: the configuration's limit, else a default by
+// the width of a cell's state (fewer stages for wider states, whose ring leaves a narrower window)
+int max_group2d_of(const eslbm_config &c, int64_t planes)
+{
+    if (c.blocking >= 2) return c.blocking;
+    return planes * (c.precision == ESLBM_FP64 ? 8 : 4) >= 48 ? 6 : 9;
+}
+
+bool blocked2d_of(const eslbm_config &c) { return c.dim == 2 && c.blocking != ESLBM_BLOCKING_OFF && c.nx % (c.precision == ESLBM_FP64 ? 2 : 4) == 0; }
+
+// Stages one launch may run: the record buffer of the diagnostics holds that many.
+int64_t max_launch_stages(const eslbm_config &c, int64_t stages_per_step, int64_t planes)
+{
+    if (c.dim == 1 && c.blocking != ESLBM_BLOCKING_OFF) return stages_per_step * fused_group_of(stages_per_step);
+    if (blocked2d_of(c)) return std::min<int64_t>(stages_per_step, std::min(max_group2d_of(c, planes), kStep2dMaxStages));
+    return 1;
+}
+
+// workspace: counters, FP64 reduction partials and totals, then the records (diagnostics)
+constexpr size_t kRecordsOffset = kCountersBytes + sizeof(double) * 6 * 1024 + 256;
 
 }  // namespace
 
@@ -89,6 +117,7 @@ struct eslbm_handle {
     {
         return reinterpret_cast<double *>(ws + kCountersBytes + sizeof(double) * 6 * (size_t)totals_blocks());
     }
+    void *records() { return ws + kRecordsOffset; }
     void *spare() { return f[1 - cur]; }
 };
 
@@ -128,6 +157,27 @@ Shift make_shift(const eslbm_handle *h, int64_t s)
     return sh;
 }
 
+// kernel parameters of a launch of `stages` stages: with diagnostics the launch records its
+// relaxations (Params::rec)
+Params launch_params(const eslbm_handle *h, int stages)
+{
+    Params P = h->P;
+    if (records_of(h->cfg)) {
+        P.rec = (uint64_t)(uintptr_t)const_cast<eslbm_handle *>(h)->records();
+        P.rec_cells = h->sz.ncell;
+        P.rec_stages = stages;
+    }
+    return P;
+}
+
+// the per-cell check of what the launch recorded (diagnostics)
+eslbm_status check_records(eslbm_handle *h, const Params &P)
+{
+    if (!P.rec) return ESLBM_OK;
+    CK(launch_check(h->family, h->fp64, h->om, P, h->counters(), h->stream), "entropy check");
+    return ESLBM_OK;
+}
+
 eslbm_status launch_one_stage(eslbm_handle *h, int64_t shift, int kind)
 {
     StageLaunch L;
@@ -139,12 +189,12 @@ eslbm_status launch_one_stage(eslbm_handle *h, int64_t shift, int kind)
     L.sh = make_shift(h, shift);
     L.kind = kind;
     L.cnt = h->counters();
-    L.P = h->P;
+    L.P = launch_params(h, 1);
     L.stream = h->stream;
-    CK(launch_stage(h->family, h->fp64, h->om, h->cfg.diagnostics != 0, L), "stage launch");
+    CK(launch_stage(h->family, h->fp64, h->om, L), "stage launch");
     h->cur = 1 - h->cur;
     h->relaxations += (uint64_t)h->sz.ncell;
-    return ESLBM_OK;
+    return check_records(h, L.P);
 }
 
 eslbm_status run_ops(eslbm_handle *h)
@@ -163,14 +213,9 @@ eslbm_status run_ops(eslbm_handle *h)
 
 // 1D runs use the temporally blocked kernel (unless blocking is off): the stages of
 // `steps` consecutive steps (merged shifts, as in run_ops) in one launch.
-bool fused_path(const eslbm_handle *h) { return h->cfg.dim == 1 && h->cfg.blocking == ESLBM_BLOCKING_AUTO; }
+bool fused_path(const eslbm_handle *h) { return h->cfg.dim == 1 && h->cfg.blocking != ESLBM_BLOCKING_OFF; }
 
-// steps fused into one launch: one composite step, or up to 24 steps of the short schemes
-int64_t fused_group(const eslbm_handle *h)
-{
-    const int64_t sps = h->sz.stages_per_step;
-    return sps >= 16 ? 1 : std::max<int64_t>(1, 24 / sps);
-}
+int64_t fused_group(const eslbm_handle *h) { return fused_group_of(h->sz.stages_per_step); }
 
 eslbm_status run_fused(eslbm_handle *h, int64_t steps)
 {
@@ -198,11 +243,98 @@ eslbm_status run_fused(eslbm_handle *h, int64_t steps)
     L.fout = h->f[1 - h->cur];
     L.n = h->cfg.nx;
     L.cnt = h->counters();
-    L.P = h->P;
+    L.P = launch_params(h, L.sl.n);
     L.stream = h->stream;
-    CK(launch_fused1d(h->family, h->fp64, h->om, h->cfg.diagnostics != 0, L), "fused step launch");
+    CK(launch_fused1d(h->family, h->fp64, h->om, L), "fused step launch");
     h->cur = 1 - h->cur;
     h->relaxations += (uint64_t)h->sz.ncell * (uint64_t)L.sl.n;
+    return check_records(h, L.P);
+}
+
+// 2D runs use the temporally blocked 2D kernel (unless blocking is off) when rows start on
+// 16-byte boundaries: the stages of a step in groups, each group one launch.
+bool blocked2d_path(const eslbm_handle *h) { return blocked2d_of(h->cfg); }
+
+int max_group2d(const eslbm_handle *h) { return max_group2d_of(h->cfg, h->sz.planes); }
+
+struct Group2d {
+    StageList sl;
+    Plan2d plan;
+};
+
+// The stages of one step from `pending` (merged shifts, as in run_ops) in groups of at most
+// max_group2d stages, split evenly; a group whose window does not fit is halved until it does.
+bool step_groups2d(const eslbm_handle *h, int64_t pending, std::vector<Group2d> &out, int64_t *pending_after)
+{
+    std::vector<std::pair<int, int>> st;  // (shift, kind)
+    for (const Op &op : h->ops) {
+        if (!op.relax) {
+            pending += op.shift;
+            continue;
+        }
+        if (pending > 64 || pending < -64) return false;
+        st.push_back({(int)pending, op.kind});
+        pending = 0;
+    }
+    *pending_after = pending;
+    out.clear();
+    const int n = (int)st.size();
+    const int gmax = std::max(1, std::min(max_group2d(h), kStep2dMaxStages));
+    const int ngroups = (n + gmax - 1) / gmax;
+    const int elem = h->fp64 ? 8 : 4;
+    const int sms = device_sms();
+    std::vector<std::pair<int, int>> spans;  // [first, count)
+    for (int g = 0, first = 0; g < ngroups; ++g) {
+        const int cnt = n / ngroups + (g < n % ngroups ? 1 : 0);
+        spans.push_back({first, cnt});
+        first += cnt;
+    }
+    for (size_t i = 0; i < spans.size(); ++i) {
+        Group2d G;
+        G.sl.n = spans[i].second;
+        G.sl.halo = 0;
+        for (int j = 0; j < G.sl.n; ++j) {
+            G.sl.shift[j] = st[(size_t)(spans[i].first + j)].first;
+            G.sl.kind[j] = st[(size_t)(spans[i].first + j)].second;
+            G.sl.halo += std::abs(G.sl.shift[j]);
+        }
+        if (plan_step2d(h->cfg.nx, h->cfg.ny, (int)h->sz.planes, elem, sms, G.sl, G.plan)) {
+            out.push_back(G);
+        } else {
+            if (G.sl.n == 1) return false;
+            const int half = G.sl.n / 2;
+            spans.insert(spans.begin() + (long)i + 1, {spans[i].first + half, G.sl.n - half});
+            spans[i].second = half;
+            --i;
+        }
+    }
+    return true;
+}
+
+eslbm_status run_blocked2d(eslbm_handle *h)
+{
+    std::vector<Group2d> groups;
+    int64_t after = 0;
+    if (!step_groups2d(h, h->pending, groups, &after)) return run_ops(h);  // one launch per stage
+    for (const Group2d &G : groups) {
+        Step2dLaunch L;
+        L.fin = h->f[h->cur];
+        L.fout = h->f[1 - h->cur];
+        L.nx = h->cfg.nx;
+        L.ny = h->cfg.ny;
+        L.ncell = h->sz.ncell;
+        L.sl = G.sl;
+        L.plan = G.plan;
+        L.cnt = h->counters();
+        L.P = launch_params(h, G.sl.n);
+        L.stream = h->stream;
+        CK(launch_step2d(h->family, h->fp64, h->om, L), "blocked 2D launch");
+        h->cur = 1 - h->cur;
+        h->relaxations += (uint64_t)h->sz.ncell * (uint64_t)G.sl.n;
+        eslbm_status s = check_records(h, L.P);
+        if (s != ESLBM_OK) return s;
+    }
+    h->pending = after;
     return ESLBM_OK;
 }
 
@@ -213,14 +345,24 @@ eslbm_status run_unit(eslbm_handle *h, int64_t steps)
 {
     if (fused_path(h)) return run_fused(h, steps);
     for (int64_t i = 0; i < steps; ++i) {
-        eslbm_status s = run_ops(h);
+        eslbm_status s = blocked2d_path(h) ? run_blocked2d(h) : run_ops(h);
         if (s != ESLBM_OK) return s;
     }
     return ESLBM_OK;
 }
 
-// buffer swaps per unit (the graph must return the ping-pong buffers to their start)
-int64_t unit_swaps(const eslbm_handle *h) { return fused_path(h) ? 1 : h->sz.stages_per_step; }
+// buffer swaps per unit from the current pending shift (the graph must return the ping-pong
+// buffers to their start)
+int64_t unit_swaps(const eslbm_handle *h)
+{
+    if (fused_path(h)) return 1;
+    if (blocked2d_path(h)) {
+        std::vector<Group2d> groups;
+        int64_t after = 0;
+        if (step_groups2d(h, h->pending, groups, &after)) return (int64_t)groups.size();
+    }
+    return h->sz.stages_per_step;
+}
 
 eslbm_status capture_graph(eslbm_handle *h)
 {
@@ -295,7 +437,7 @@ eslbm_status stage_between(eslbm_handle *h, const void *fin, void *fout, int64_t
     L.cnt = h->counters();
     L.P = h->P;
     L.stream = h->stream;
-    CK(launch_stage(h->family, h->fp64, h->om, false, L), "stage launch");
+    CK(launch_stage(h->family, h->fp64, h->om, L), "stage launch");
     return ESLBM_OK;
 }
 
@@ -390,7 +532,7 @@ eslbm_status eslbm_gradient(eslbm_handle *h, const double *u0, const double *dJ_
                 L.rec = stage(0);
                 L.rec_stride_bytes = (int64_t)G.stride;
                 L.nrec = L.sl.n - 1;
-                CK(launch_fused1d(h->family, h->fp64, h->om, false, L), "recording step launch");
+                CK(launch_fused1d(h->family, h->fp64, h->om, L), "recording step launch");
             } else {
                 for (const Op &op : h->ops) {
                     if (!op.relax) {
@@ -456,11 +598,32 @@ eslbm_status eslbm_query(const eslbm_config *cfg, eslbm_sizes *out)
     z.planes = z.q * z.M;
     z.ncell = cfg->nx * cfg->ny;
     z.state_bytes = (uint64_t)z.planes * (uint64_t)z.ncell * (cfg->precision == ESLBM_FP64 ? 8u : 4u);
-    z.workspace_bytes = kCountersBytes + sizeof(double) * 6 * (uint64_t)totals_blocks() + 256;
     int64_t stages = 0;
     for (const Op &op : scheme_ops(cfg->scheme, cfg->kappa)) stages += op.relax ? 1 : 0;
     z.stages_per_step = stages;
+    static_assert(kRecordsOffset == kCountersBytes + sizeof(double) * 6 * 1024 + 256, "workspace layout");
+    z.workspace_bytes = kRecordsOffset;
+    if (records_of(*cfg))  // diagnostics: one record of every relaxation of a launch
+        z.workspace_bytes += (uint64_t)record_fields((int)z.q, (int)z.M) *
+                             (uint64_t)max_launch_stages(*cfg, stages, z.planes) * (uint64_t)z.ncell *
+                             (cfg->precision == ESLBM_FP64 ? 8u : 4u);
     z.step_cells = step_cells(cfg->scheme, cfg->kappa);
+    z.launches_per_step = (double)stages;
+    if (cfg->dim == 1 && cfg->blocking != ESLBM_BLOCKING_OFF) {
+        z.launches_per_step = 1.0 / (double)fused_group_of(stages);
+    } else if (blocked2d_of(*cfg)) {
+        eslbm_handle probe;  // the grouping needs the configuration, sizes and operator list only
+        probe.cfg = *cfg;
+        probe.sz = z;
+        probe.fp64 = cfg->precision == ESLBM_FP64;
+        probe.ops = scheme_ops(cfg->scheme, cfg->kappa);
+        int64_t pend = 0;
+        for (const Op &op : probe.ops)  // the trailing shift that a step leaves pending
+            pend = op.relax ? 0 : pend + op.shift;
+        std::vector<Group2d> groups;
+        int64_t after = 0;
+        if (step_groups2d(&probe, pend, groups, &after)) z.launches_per_step = (double)groups.size();
+    }
     *out = z;
     return ESLBM_OK;
 }

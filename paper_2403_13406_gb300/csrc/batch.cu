@@ -26,7 +26,7 @@ uint64_t align256(uint64_t b) { return (b + 255u) / 256u * 256u; }
 
 struct Layout {
     int64_t q, M, planes, total_cells, max_items;
-    uint64_t elem, pool_bytes, inst_off, items_off, handle_ws_off, handle_ws_bytes, ws_bytes;
+    uint64_t elem, pool_bytes, inst_off, items_off, handle_ws_off, handle_ws_bytes, rec_off, ws_bytes;
     std::vector<BatchInstance> inst;
 };
 
@@ -37,7 +37,7 @@ eslbm_status layout(const eslbm_config *base, int32_t count, const int64_t *nx, 
     L.inst.resize((size_t)count);
     L.total_cells = 0;
     L.max_items = 0;
-    uint64_t off = 0;
+    uint64_t off = 0, handle_ws = 0;
     eslbm_sizes sz{};
     for (int32_t i = 0; i < count; ++i) {
         eslbm_config c = *base;
@@ -47,8 +47,9 @@ eslbm_status layout(const eslbm_config *base, int32_t count, const int64_t *nx, 
         if (s != ESLBM_OK) return s;
         if (nx[i] > INT32_MAX) return ESLBM_ERR_ARG;  // work items hold 32-bit columns
         L.elem = base->precision == ESLBM_FP64 ? 8 : 4;
-        L.inst[(size_t)i] = {nx[i], ny[i], (int64_t)(off / L.elem)};
+        L.inst[(size_t)i] = {nx[i], ny[i], (int64_t)(off / L.elem), L.total_cells};
         off += align256(sz.state_bytes);
+        handle_ws = std::max<uint64_t>(handle_ws, sz.workspace_bytes);
         L.total_cells += sz.ncell;
         L.max_items += ny[i] * ((nx[i] + kMinSegment - 1) / kMinSegment);
     }
@@ -60,8 +61,12 @@ eslbm_status layout(const eslbm_config *base, int32_t count, const int64_t *nx, 
     L.inst_off = kCounters;
     L.items_off = L.inst_off + align256(sizeof(BatchInstance) * (uint64_t)count);
     L.handle_ws_off = L.items_off + align256(sizeof(BatchItem) * (uint64_t)L.max_items);
-    L.handle_ws_bytes = align256(sz.workspace_bytes);
-    L.ws_bytes = L.handle_ws_off + L.handle_ws_bytes;
+    L.handle_ws_bytes = align256(handle_ws);
+    L.rec_off = L.handle_ws_off + L.handle_ws_bytes;
+    L.ws_bytes = L.rec_off;
+    if (records_of(*base))  // diagnostics: one record of every relaxation of a step of every instance
+        L.ws_bytes += (uint64_t)record_fields((int)L.q, (int)L.M) * (uint64_t)sz.stages_per_step *
+                      (uint64_t)L.total_cells * L.elem;
     return ESLBM_OK;
 }
 
@@ -188,10 +193,16 @@ eslbm_status run_step(eslbm_batch *b)
     B.side = b->side;
     B.cnt = b->counters();
     B.P = b->P;
+    if (records_of(b->cfg)) {  // diagnostics: record every relaxation, then check the records
+        B.P.rec = (uint64_t)(uintptr_t)(b->ws + b->L.rec_off);
+        B.P.rec_cells = b->L.total_cells;
+        B.P.rec_stages = B.sl.n;
+    }
     B.grid = std::max(1, std::min(b->n_items, b->sms * b->blocks_per_sm));
     B.stream = b->stream;
-    BCK(launch_batch_step(b->family, b->fp64, b->om, b->cfg.diagnostics != 0, B), "batch step launch");
+    BCK(launch_batch_step(b->family, b->fp64, b->om, B), "batch step launch");
     if (B.sl.n & 1) b->side ^= 1;
+    if (B.P.rec) BCK(launch_check(b->family, b->fp64, b->om, B.P, b->counters(), b->stream), "entropy check");
     return ESLBM_OK;
 }
 
@@ -286,7 +297,7 @@ eslbm_status eslbm_batch_create(const eslbm_config *base, int32_t count, const i
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-    b->max_bps = batch_blocks_per_sm(b->family, b->fp64, b->om, b->cfg.diagnostics != 0);
+    b->max_bps = batch_blocks_per_sm(b->family, b->fp64, b->om);
     if (b->sms < 1 || b->max_bps < 1) {
         delete b;
         return ESLBM_ERR_CUDA;

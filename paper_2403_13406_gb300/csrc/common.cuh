@@ -27,6 +27,16 @@ struct Params {
     int shifted;
     double fbar[16], ubar[4], cm[4], rdev[16];
     double aux[4];  // reference quantities of the deviation forms (velocities, pressure)
+    // Diagnostics: when rec is set (a device buffer in the storage precision), an
+    // entropic kernel records the inputs of every relaxation it performs -- the
+    // moments u (M values), the deviations delta (q M) and the omega used -- at
+    // rec[((i * rec_stages) + stage) * rec_cells + cell] for field i, and a separate
+    // kernel checks them (k_check).  Recording only stores values the relaxation
+    // holds anyway, behind a uniform branch: the arithmetic is the same with and
+    // without it.  A projection records omega = 1 only.
+    uint64_t rec;
+    int64_t rec_cells;
+    int rec_stages;
 };
 
 // The same parameters in the arithmetic type of a kernel (converted once on the
@@ -37,6 +47,9 @@ template <class R> struct ParamsR {
     R gV4, inv16gV;  // 4 g V and 1 / (16 g V) (shallow water)
     int shifted;     // see Params
     R ubar[4], cm[4], rdev[16], fbar[16], aux[4];
+    R *rec;          // see Params
+    int64_t rec_cells;
+    int rec_stages;
 };
 
 template <class R> inline ParamsR<R> params_as(const Params &P)
@@ -55,6 +68,9 @@ template <class R> inline ParamsR<R> params_as(const Params &P)
     q.gV4 = R(4.0 * P.g * P.V);
     q.inv16gV = P.g > 0 ? R(1.0 / (16.0 * P.g * P.V)) : R(0);
     q.shifted = P.shifted;
+    q.rec = reinterpret_cast<R *>(P.rec);
+    q.rec_cells = P.rec_cells;
+    q.rec_stages = P.rec_stages;
     for (int i = 0; i < 4; ++i) {
         q.ubar[i] = R(P.ubar[i]);
         q.cm[i] = R(P.cm[i]);
@@ -105,6 +121,38 @@ struct StageList {
     int kind[kMaxFusedStages];   // KIND_MAIN or KIND_PROJECT
 };
 
+// Limits of the temporally blocked 2D kernel (k_step2d): threads of a block,
+// stages of one launch, rows of the ring (one mbarrier each, at the start of the
+// dynamic shared memory) and dynamic shared memory of a block (227 KB per block
+// on sm_103, less 2 KB for the kernel's static arrays).
+#ifndef ESLBM_STEP2D_BLOCKS_PER_SM
+#define ESLBM_STEP2D_BLOCKS_PER_SM 1
+#endif
+#ifndef ESLBM_STEP2D_PREFETCH
+#define ESLBM_STEP2D_PREFETCH 3
+#endif
+#ifndef ESLBM_STEP2D_THREADS
+#define ESLBM_STEP2D_THREADS 768
+#endif
+constexpr int kStep2dThreads = ESLBM_STEP2D_THREADS;             // threads of a block (most variants)
+constexpr int kStep2dSlots = 8;                                   // items (stage, column) a thread owns
+constexpr int kStep2dMaxItems = kStep2dSlots * 256;               // items of a tick (smallest block: 256)
+constexpr int kStep2dBlocksPerSm = ESLBM_STEP2D_BLOCKS_PER_SM;  // resident blocks per SM (shared memory split)
+constexpr int kStep2dPrefetch = ESLBM_STEP2D_PREFETCH;          // window rows loaded ahead of use
+constexpr int kStep2dMaxStages = 32;
+constexpr int kStep2dMaxRing = 64;
+constexpr int kStep2dBarBytes = 8 * kStep2dMaxRing;
+constexpr int kStep2dSmemBudget = 232448 / kStep2dBlocksPerSm - 2048;
+
+// Launch plan of the temporally blocked 2D kernel (k_step2d) for one group of
+// stages: a block owns tx x ly output cells and keeps `ring` rows of a window
+// tx + 2 hl wide in shared memory (see step2d.cuh).
+struct Plan2d {
+    int tx, ly, hl, wx, ring, prefetch, nstrips, nsegs;
+    int items;    // (stage, column) items of a tick: sum over the stages of tx + 2 (H - m_j)
+    size_t smem;  // dynamic shared memory bytes
+};
+
 inline bool stage_list_ok(const StageList &sl)
 {
     if (sl.n < 1 || sl.n > kMaxFusedStages) return false;
@@ -118,6 +166,7 @@ inline bool stage_list_ok(const StageList &sl)
 struct BatchInstance {
     int64_t nx, ny;
     int64_t offset;  // element offset of the instance's first plane in the pool
+    int64_t cell0;   // index of the instance's first cell among the cells of all instances
 };
 struct BatchItem {
     int32_t inst;    // instance

@@ -1,14 +1,15 @@
 // fam_misc.cu -- Euler (fixed omega), gathers, conversion and the dispatch
 // entry points declared in launch.h.
+#include <algorithm>
 #include <cmath>
 
 #include "family_impl.cuh"
 
 namespace eslbm {
 
-cudaError_t stage_scalar(int, bool, int, bool, const StageLaunch &);
-cudaError_t stage_sw1(bool, int, bool, const StageLaunch &);
-cudaError_t stage_sw2(bool, int, bool, const StageLaunch &);
+cudaError_t stage_scalar(int, bool, int, const StageLaunch &);
+cudaError_t stage_sw1(bool, int, const StageLaunch &);
+cudaError_t stage_sw2(bool, int, const StageLaunch &);
 cudaError_t init_scalar(int, bool, const double *, void *, int64_t, const Params &, Counters *, cudaStream_t);
 cudaError_t init_sw1(bool, const double *, void *, int64_t, const Params &, Counters *, cudaStream_t);
 cudaError_t init_sw2(bool, const double *, void *, int64_t, const Params &, Counters *, cudaStream_t);
@@ -19,22 +20,34 @@ cudaError_t totals_sw1(bool, const void *, double *, double *, int64_t, int64_t,
 cudaError_t totals_sw2(bool, const void *, double *, double *, int64_t, int64_t, const Shift &, const Params &,
                        cudaStream_t);
 
-cudaError_t fused_scalar(int, bool, int, bool, const FusedLaunch &);
-cudaError_t fused_sw1(bool, int, bool, const FusedLaunch &);
+cudaError_t stage_euler(bool, const StageLaunch &);
+cudaError_t step2d_euler(bool, const Step2dLaunch &);
+cudaError_t step2d_scalar(int, bool, int, const Step2dLaunch &);
+cudaError_t step2d_sw2(bool, int, const Step2dLaunch &);
+cudaError_t init_euler(bool, const double *, void *, int64_t, const Params &, Counters *, cudaStream_t);
+cudaError_t totals_euler(bool, const void *, double *, double *, int64_t, int64_t, const Shift &, const Params &,
+                         cudaStream_t);
+cudaError_t adjoint_euler(bool, const AdjointLaunch &);
+cudaError_t adjoint_init_euler(bool, const double *, const void *, double *, int64_t, const Params &, cudaStream_t);
+cudaError_t batch_euler(bool, const BatchLaunch &);
+int batch_occ_euler(bool);
 
-cudaError_t launch_fused1d(int family, bool fp64, int om, bool diag, const FusedLaunch &L)
+cudaError_t fused_scalar(int, bool, int, const FusedLaunch &);
+cudaError_t fused_sw1(bool, int, const FusedLaunch &);
+
+cudaError_t launch_fused1d(int family, bool fp64, int om, const FusedLaunch &L)
 {
-    if (family == FAM_SW1) return fused_sw1(fp64, om, diag, L);
-    if (family == FAM_LINEAR1 || family == FAM_BURGERS1) return fused_scalar(family, fp64, om, diag, L);
+    if (family == FAM_SW1) return fused_sw1(fp64, om, L);
+    if (family == FAM_LINEAR1 || family == FAM_BURGERS1) return fused_scalar(family, fp64, om, L);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_stage(int family, bool fp64, int om, bool diag, const StageLaunch &L)
+cudaError_t launch_stage(int family, bool fp64, int om, const StageLaunch &L)
 {
-    if (family == FAM_SW1) return stage_sw1(fp64, om, diag, L);
-    if (family == FAM_SW2) return stage_sw2(fp64, om, diag, L);
-    if (family == FAM_EULER2) return stage_family<Euler2, 2>(fp64, OM_FIXED, false, L);
-    return stage_scalar(family, fp64, om, diag, L);
+    if (family == FAM_SW1) return stage_sw1(fp64, om, L);
+    if (family == FAM_SW2) return stage_sw2(fp64, om, L);
+    if (family == FAM_EULER2) return stage_euler(fp64, L);
+    return stage_scalar(family, fp64, om, L);
 }
 
 cudaError_t launch_init_eq(int family, bool fp64, const double *u0, void *f, int64_t ncell, const Params &P,
@@ -42,7 +55,7 @@ cudaError_t launch_init_eq(int family, bool fp64, const double *u0, void *f, int
 {
     if (family == FAM_SW1) return init_sw1(fp64, u0, f, ncell, P, cnt, st);
     if (family == FAM_SW2) return init_sw2(fp64, u0, f, ncell, P, cnt, st);
-    if (family == FAM_EULER2) return init_family<Euler2>(fp64, u0, f, ncell, P, cnt, st);
+    if (family == FAM_EULER2) return init_euler(fp64, u0, f, ncell, P, cnt, st);
     return init_scalar(family, fp64, u0, f, ncell, P, cnt, st);
 }
 
@@ -51,7 +64,7 @@ cudaError_t launch_totals(int family, bool fp64, const void *f, double *partials
 {
     if (family == FAM_SW1) return totals_sw1(fp64, f, partials, out, nx, ny, sh, P, st);
     if (family == FAM_SW2) return totals_sw2(fp64, f, partials, out, nx, ny, sh, P, st);
-    if (family == FAM_EULER2) return totals_family<Euler2, 2>(fp64, f, partials, out, nx, ny, sh, P, st);
+    if (family == FAM_EULER2) return totals_euler(fp64, f, partials, out, nx, ny, sh, P, st);
     return totals_scalar(family, fp64, f, partials, out, nx, ny, sh, P, st);
 }
 
@@ -184,7 +197,7 @@ cudaError_t launch_adjoint_stage(int family, bool fp64, int om, const AdjointLau
 {
     if (family == FAM_SW1) return adjoint_sw1(fp64, om, L);
     if (family == FAM_SW2) return adjoint_sw2(fp64, om, L);
-    if (family == FAM_EULER2) return adjoint_family<Euler2, 2>(fp64, OM_FIXED, L);
+    if (family == FAM_EULER2) return adjoint_euler(fp64, L);
     return adjoint_scalar(family, fp64, om, L);
 }
 
@@ -193,7 +206,7 @@ cudaError_t launch_adjoint_init(int family, bool fp64, const double *u0, const v
 {
     if (family == FAM_SW1) return adjoint_init_sw1(fp64, u0, g, du0, ncell, P, st);
     if (family == FAM_SW2) return adjoint_init_sw2(fp64, u0, g, du0, ncell, P, st);
-    if (family == FAM_EULER2) return adjoint_init_family<Euler2>(fp64, u0, g, du0, ncell, P, st);
+    if (family == FAM_EULER2) return adjoint_init_euler(fp64, u0, g, du0, ncell, P, st);
     return adjoint_init_scalar(family, fp64, u0, g, du0, ncell, P, st);
 }
 
@@ -211,25 +224,119 @@ cudaError_t launch_adjoint_readout(int dim, bool fp64, const double *lam, void *
     return cudaGetLastError();
 }
 
-cudaError_t batch_scalar(int, bool, int, bool, const BatchLaunch &);
-cudaError_t batch_sw2(bool, int, bool, const BatchLaunch &);
-int batch_occ_scalar(int, bool, int, bool);
-int batch_occ_sw2(bool, int, bool);
+cudaError_t batch_scalar(int, bool, int, const BatchLaunch &);
+cudaError_t batch_sw2(bool, int, const BatchLaunch &);
+int batch_occ_scalar(int, bool, int);
+int batch_occ_sw2(bool, int);
 
-cudaError_t launch_batch_step(int family, bool fp64, int om, bool diag, const BatchLaunch &L)
+cudaError_t launch_batch_step(int family, bool fp64, int om, const BatchLaunch &L)
 {
-    if (family == FAM_SW2) return batch_sw2(fp64, om, diag, L);
-    if (family == FAM_EULER2) return batch_family<Euler2>(fp64, OM_FIXED, false, L);
-    if (family == FAM_LINEAR2 || family == FAM_BURGERS2) return batch_scalar(family, fp64, om, diag, L);
+    if (family == FAM_SW2) return batch_sw2(fp64, om, L);
+    if (family == FAM_EULER2) return batch_euler(fp64, L);
+    if (family == FAM_LINEAR2 || family == FAM_BURGERS2) return batch_scalar(family, fp64, om, L);
     return cudaErrorInvalidValue;
 }
 
-int batch_blocks_per_sm(int family, bool fp64, int om, bool diag)
+int batch_blocks_per_sm(int family, bool fp64, int om)
 {
-    if (family == FAM_SW2) return batch_occ_sw2(fp64, om, diag);
-    if (family == FAM_EULER2) return batch_occ_family<Euler2>(fp64, OM_FIXED, false);
-    if (family == FAM_LINEAR2 || family == FAM_BURGERS2) return batch_occ_scalar(family, fp64, om, diag);
+    if (family == FAM_SW2) return batch_occ_sw2(fp64, om);
+    if (family == FAM_EULER2) return batch_occ_euler(fp64);
+    if (family == FAM_LINEAR2 || family == FAM_BURGERS2) return batch_occ_scalar(family, fp64, om);
     return 0;
+}
+
+cudaError_t check_sw1(bool, int, const Params &, Counters *, cudaStream_t);
+cudaError_t check_sw2(bool, int, const Params &, Counters *, cudaStream_t);
+cudaError_t check_scalar(int, bool, int, const Params &, Counters *, cudaStream_t);
+
+cudaError_t launch_check(int family, bool fp64, int om, const Params &P, Counters *cnt, cudaStream_t st)
+{
+    if (family == FAM_SW1) return check_sw1(fp64, om, P, cnt, st);
+    if (family == FAM_SW2) return check_sw2(fp64, om, P, cnt, st);
+    return check_scalar(family, fp64, om, P, cnt, st);
+}
+
+cudaError_t launch_step2d(int family, bool fp64, int om, const Step2dLaunch &L)
+{
+    if (family == FAM_SW2) return step2d_sw2(fp64, om, L);
+    if (family == FAM_EULER2) return step2d_euler(fp64, L);
+    if (family == FAM_LINEAR2 || family == FAM_BURGERS2) return step2d_scalar(family, fp64, om, L);
+    return cudaErrorInvalidValue;
+}
+
+int device_sms()
+{
+    static std::atomic<int> sm_count[kMaxDevices];
+    const int d = device_slot();
+    int sms = sm_count[d].load();
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+            (void)cudaGetLastError();  // no device (host-only use): plan for one SM, leave no error behind
+            return 1;
+        }
+        sm_count[d].store(sms);
+    }
+    return sms;
+}
+
+bool plan_step2d(int64_t nx, int64_t ny, int planes, int elem, int sms, const StageList &sl, Plan2d &pl)
+{
+    if (!stage_list_ok(sl) || sl.n > kStep2dMaxStages || planes < 1 || (elem != 4 && elem != 8)) return false;
+    const int V4 = 16 / elem;
+    if (nx % V4) return false;
+    const int H = sl.halo;
+    // lags of the stages behind the load, and the ring that keeps every slot until its last reader
+    int lag = 0, acc = 0, E = 0;
+    int64_t items_margin = 0;
+    int m = 0;
+    for (int j = 0; j < sl.n; ++j) {
+        const int s = sl.shift[j], as = s < 0 ? -s : s;
+        lag += as + (j > 0 ? 1 : 0);
+        acc += s;
+        m += as;
+        E = std::max(E, lag + (acc < 0 ? -acc : acc));
+        items_margin += 2 * (H - m);
+    }
+    pl.prefetch = kStep2dPrefetch;
+    pl.ring = E + pl.prefetch;
+    if (pl.ring > kStep2dMaxRing) return false;
+    pl.hl = (H + V4 - 1) / V4 * V4;
+    const int64_t budget = kStep2dSmemBudget - kStep2dBarBytes;
+    const int wx_max = (int)(budget / ((int64_t)pl.ring * planes * elem)) / V4 * V4;
+    const int tx_max = wx_max - 2 * pl.hl;
+    // a tick's items (about n tx) must fit the slots of the smallest block
+    const int tx_cap = (int)std::min<int64_t>(tx_max, (kStep2dMaxItems - items_margin) / sl.n / V4 * V4);
+    if (tx_cap < std::max(4 * V4, pl.hl)) return false;
+    // strips as wide as the window allows, evened out over the row
+    int64_t nstrips = (nx + tx_cap - 1) / tx_cap;
+    const int64_t even = (nx + nstrips - 1) / nstrips;
+    pl.tx = (int)((even + V4 - 1) / V4 * V4);
+    nstrips = (nx + pl.tx - 1) / pl.tx;
+    pl.nstrips = (int)nstrips;
+    pl.wx = pl.tx + 2 * pl.hl;
+    // rows per block: the time is (waves of kStep2dBlocksPerSm blocks per SM) x (ticks of a block)
+    static const int cand[] = {32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096, 8192};
+    double best = 0.0;
+    pl.ly = 0;
+    for (int ly : cand) {
+        const int lye = (int)std::min<int64_t>(ly, ny);
+        const int64_t nsegs = (ny + lye - 1) / lye;
+        const int64_t blocks = nstrips * nsegs;
+        const int64_t waves = (blocks + (int64_t)sms * kStep2dBlocksPerSm - 1) / ((int64_t)sms * kStep2dBlocksPerSm);
+        const double cost = (double)waves * (double)(lye + H + lag);
+        if (pl.ly == 0 || cost < best) {
+            best = cost;
+            pl.ly = lye;
+            pl.nsegs = (int)nsegs;
+        }
+        if (ly >= ny) break;
+    }
+    if ((int64_t)pl.nstrips * pl.nsegs > 0x7fffffffLL) return false;
+    pl.items = (int)((int64_t)sl.n * pl.tx + items_margin);
+    pl.smem = (size_t)kStep2dBarBytes + (size_t)pl.ring * planes * pl.wx * elem;
+    return pl.smem <= (size_t)kStep2dSmemBudget;
 }
 
 int totals_blocks() { return kRedBlocks; }

@@ -3,21 +3,28 @@
 
 namespace eslbm {
 
-cudaError_t stage_scalar(int family, bool fp64, int om, bool diag, const StageLaunch &L)
+cudaError_t stage_scalar(int family, bool fp64, int om, const StageLaunch &L)
 {
     switch (family) {
-    case FAM_LINEAR1: return stage_family<Scalar<1, false>, 1>(fp64, om, diag, L);
-    case FAM_LINEAR2: return stage_family<Scalar<2, false>, 2>(fp64, om, diag, L);
-    case FAM_BURGERS1: return stage_family<Scalar<1, true>, 1>(fp64, om, diag, L);
-    case FAM_BURGERS2: return stage_family<Scalar<2, true>, 2>(fp64, om, diag, L);
+    case FAM_LINEAR1: return stage_family<Scalar<1, false>, 1>(fp64, om, L);
+    case FAM_LINEAR2: return stage_family<Scalar<2, false>, 2>(fp64, om, L);
+    case FAM_BURGERS1: return stage_family<Scalar<1, true>, 1>(fp64, om, L);
+    case FAM_BURGERS2: return stage_family<Scalar<2, true>, 2>(fp64, om, L);
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t fused_scalar(int family, bool fp64, int om, bool diag, const FusedLaunch &L)
+cudaError_t step2d_scalar(int family, bool fp64, int om, const Step2dLaunch &L)
 {
-    if (family == FAM_LINEAR1) return fused_family<Scalar<1, false>>(fp64, om, diag, L);
-    if (family == FAM_BURGERS1) return fused_family<Scalar<1, true>>(fp64, om, diag, L);
+    if (family == FAM_LINEAR2) return step2d_family<Scalar<2, false>>(fp64, om, L);
+    if (family == FAM_BURGERS2) return step2d_family<Scalar<2, true>>(fp64, om, L);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t fused_scalar(int family, bool fp64, int om, const FusedLaunch &L)
+{
+    if (family == FAM_LINEAR1) return fused_family<Scalar<1, false>>(fp64, om, L);
+    if (family == FAM_BURGERS1) return fused_family<Scalar<1, true>>(fp64, om, L);
     return cudaErrorInvalidValue;
 }
 
@@ -44,17 +51,17 @@ cudaError_t adjoint_init_scalar(int family, bool fp64, const double *u0, const v
     return cudaErrorInvalidValue;
 }
 
-cudaError_t batch_scalar(int family, bool fp64, int om, bool diag, const BatchLaunch &L)
+cudaError_t batch_scalar(int family, bool fp64, int om, const BatchLaunch &L)
 {
-    if (family == FAM_LINEAR2) return batch_family<Scalar<2, false>>(fp64, om, diag, L);
-    if (family == FAM_BURGERS2) return batch_family<Scalar<2, true>>(fp64, om, diag, L);
+    if (family == FAM_LINEAR2) return batch_family<Scalar<2, false>>(fp64, om, L);
+    if (family == FAM_BURGERS2) return batch_family<Scalar<2, true>>(fp64, om, L);
     return cudaErrorInvalidValue;
 }
 
-int batch_occ_scalar(int family, bool fp64, int om, bool diag)
+int batch_occ_scalar(int family, bool fp64, int om)
 {
-    if (family == FAM_LINEAR2) return batch_occ_family<Scalar<2, false>>(fp64, om, diag);
-    if (family == FAM_BURGERS2) return batch_occ_family<Scalar<2, true>>(fp64, om, diag);
+    if (family == FAM_LINEAR2) return batch_occ_family<Scalar<2, false>>(fp64, om);
+    if (family == FAM_BURGERS2) return batch_occ_family<Scalar<2, true>>(fp64, om);
     return 0;
 }
 
@@ -80,6 +87,13 @@ cudaError_t totals_scalar(int family, bool fp64, const void *f, double *partials
     case FAM_BURGERS2: return totals_family<Scalar<2, true>, 2>(fp64, f, partials, out, nx, ny, sh, P, st);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t check_scalar(int family, bool fp64, int om, const Params &P, Counters *cnt, cudaStream_t st)
+{
+    if (family == FAM_BURGERS1) return check_family<Scalar<1, true>>(fp64, om, P, cnt, st);
+    if (family == FAM_BURGERS2) return check_family<Scalar<2, true>>(fp64, om, P, cnt, st);
+    return cudaSuccess;
 }
 
 }  // namespace eslbm

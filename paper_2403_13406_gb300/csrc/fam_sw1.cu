@@ -3,14 +3,14 @@
 
 namespace eslbm {
 
-cudaError_t stage_sw1(bool fp64, int om, bool diag, const StageLaunch &L)
+cudaError_t stage_sw1(bool fp64, int om, const StageLaunch &L)
 {
-    return stage_family<ShallowWater<1>, 1>(fp64, om, diag, L);
+    return stage_family<ShallowWater<1>, 1>(fp64, om, L);
 }
 
-cudaError_t fused_sw1(bool fp64, int om, bool diag, const FusedLaunch &L)
+cudaError_t fused_sw1(bool fp64, int om, const FusedLaunch &L)
 {
-    return fused_family<ShallowWater<1>>(fp64, om, diag, L);
+    return fused_family<ShallowWater<1>>(fp64, om, L);
 }
 
 cudaError_t adjoint_sw1(bool fp64, int om, const AdjointLaunch &L)
@@ -34,6 +34,11 @@ cudaError_t totals_sw1(bool fp64, const void *f, double *partials, double *out, 
                        const Shift &sh, const Params &P, cudaStream_t st)
 {
     return totals_family<ShallowWater<1>, 1>(fp64, f, partials, out, nx, ny, sh, P, st);
+}
+
+cudaError_t check_sw1(bool fp64, int om, const Params &P, Counters *cnt, cudaStream_t st)
+{
+    return check_family<ShallowWater<1>>(fp64, om, P, cnt, st);
 }
 
 }  // namespace eslbm

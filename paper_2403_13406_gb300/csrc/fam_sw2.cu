@@ -3,9 +3,14 @@
 
 namespace eslbm {
 
-cudaError_t stage_sw2(bool fp64, int om, bool diag, const StageLaunch &L)
+cudaError_t stage_sw2(bool fp64, int om, const StageLaunch &L)
 {
-    return stage_family<ShallowWater<2>, 2>(fp64, om, diag, L);
+    return stage_family<ShallowWater<2>, 2>(fp64, om, L);
+}
+
+cudaError_t step2d_sw2(bool fp64, int om, const Step2dLaunch &L)
+{
+    return step2d_family<ShallowWater<2>>(fp64, om, L);
 }
 
 cudaError_t adjoint_sw2(bool fp64, int om, const AdjointLaunch &L)
@@ -19,12 +24,12 @@ cudaError_t adjoint_init_sw2(bool fp64, const double *u0, const void *g, double 
     return adjoint_init_family<ShallowWater<2>>(fp64, u0, g, du0, ncell, P, st);
 }
 
-cudaError_t batch_sw2(bool fp64, int om, bool diag, const BatchLaunch &L)
+cudaError_t batch_sw2(bool fp64, int om, const BatchLaunch &L)
 {
-    return batch_family<ShallowWater<2>>(fp64, om, diag, L);
+    return batch_family<ShallowWater<2>>(fp64, om, L);
 }
 
-int batch_occ_sw2(bool fp64, int om, bool diag) { return batch_occ_family<ShallowWater<2>>(fp64, om, diag); }
+int batch_occ_sw2(bool fp64, int om) { return batch_occ_family<ShallowWater<2>>(fp64, om); }
 
 cudaError_t init_sw2(bool fp64, const double *u0, void *f, int64_t ncell, const Params &P, Counters *cnt,
                      cudaStream_t st)
@@ -36,6 +41,11 @@ cudaError_t totals_sw2(bool fp64, const void *f, double *partials, double *out, 
                        const Shift &sh, const Params &P, cudaStream_t st)
 {
     return totals_family<ShallowWater<2>, 2>(fp64, f, partials, out, nx, ny, sh, P, st);
+}
+
+cudaError_t check_sw2(bool fp64, int om, const Params &P, Counters *cnt, cudaStream_t st)
+{
+    return check_family<ShallowWater<2>>(fp64, om, P, cnt, st);
 }
 
 }  // namespace eslbm

@@ -104,6 +104,14 @@ inline int omega_mode_of(const eslbm_config &c)
     return c.precision == ESLBM_FP32_MIXED ? OM_MIXED : OM_ENTROPIC;
 }
 
+// Whether launches record their relaxations for the per-cell check (diagnostics on an
+// entropic nonlinear system).
+inline bool records_of(const eslbm_config &c)
+{
+    return c.diagnostics && c.omega_mode == ESLBM_OMEGA_ENTROPIC &&
+           (c.system == ESLBM_BURGERS || c.system == ESLBM_SHALLOW_WATER);
+}
+
 inline int64_t num_M(const eslbm_config &c)
 {
     if (c.system == ESLBM_SHALLOW_WATER) return c.dim + 1;

@@ -82,7 +82,8 @@ __device__ __forceinline__ void moments_target(const ParamsR<R> &P, const R *f, 
 }
 
 // The kernel's constants in double precision, exactly as the kernel rounded them
-// (a float kernel's g, 1 / (2V), ... promoted), for the diagnostics' FP64 check.
+// (a float kernel's g, 1 / (2V), ... promoted), for the FP64 evaluations of the
+// mixed mode and of the diagnostics.
 template <class R> __device__ __forceinline__ ParamsR<double> promote(const ParamsR<R> &p)
 {
     ParamsR<double> q;
@@ -99,6 +100,9 @@ template <class R> __device__ __forceinline__ ParamsR<double> promote(const Para
     q.gV4 = p.gV4;
     q.inv16gV = p.inv16gV;
     q.shifted = p.shifted;
+    q.rec = nullptr;
+    q.rec_cells = 0;
+    q.rec_stages = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         q.ubar[i] = p.ubar[i];
@@ -111,41 +115,6 @@ template <class R> __device__ __forceinline__ ParamsR<double> promote(const Para
         q.fbar[i] = p.fbar[i];
     }
     return q;
-}
-
-// Per-cell check of Section 4 (diagnostics): the change of the cell's microscopic
-// entropy under R_omega, F(omega - 1) = B(omega - 1) - B(-1) with
-// B(t) = sum_k B_k(t delta_k), evaluated in double precision from the moments and
-// deviations the relaxation used and the kernel's own constants.  Returns
-// F / B(-1): -1 for the projection omega = 1, 0 at equilibrium, +inf if a
-// non-trivial omega lies outside the convexity domain.
-template <class Sys, class R>
-__device__ float entropy_excess(const ParamsR<R> &P, const R *u, const R *delta, R w)
-{
-    constexpr int Q = Sys::Q, M = Sys::M;
-    if (w == R(1)) return -1.0f;
-    const ParamsR<double> Pd = promote(P);
-    double ud[M], dd[Q * M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) ud[m] = double(u[m]);
-#pragma unroll
-    for (int i = 0; i < Q * M; ++i) dd[i] = double(delta[i]);
-    typename Sys::template Ctx<double> cx;
-    Sys::template prepare<double>(Pd, ud, dd, cx);
-    double B0, d0, B1, d1;
-    if (!Sys::template eval<double>(Pd, cx, -1.0, B0, d0)) return INFINITY;
-    if (!(B0 > 0.0)) return 0.0f;
-    if (!Sys::template eval<double>(Pd, cx, double(w) - 1.0, B1, d1)) return INFINITY;
-    const double r = (B1 - B0) / B0;
-    return r == r ? float(r) : INFINITY;
-}
-
-// A per-cell entropy increase: F(omega - 1) above the rounding level of the
-// arithmetic that chose omega (FP32, or FP64 for the FP64 storage and the mixed
-// mode), 64 unit roundoffs of B(-1).
-template <class R, int OM> __device__ __forceinline__ bool entropy_increase(float excess)
-{
-    return excess > (sizeof(R) == 4 && OM != OM_MIXED ? 64.0f * 1.1920929e-7f : 64.0f * 2.220446e-16f);
 }
 
 // Entropic omega with the entropy difference in FP64 (FP32 storage).  The FP32
@@ -192,49 +161,19 @@ __device__ R mixed_omega(const ParamsR<R> &P, const R *u, const R *delta, R w, b
     }
 }
 
-// Diagnostics accumulated by a thread over its cells, merged per warp into the
-// device counters at the end of a kernel (every lane of the warp must call flush).
-struct DiagAcc {
-    float wmin, wmax, excess;
-    __device__ DiagAcc() : wmin(INFINITY), wmax(0.0f), excess(0.0f) {}
-    __device__ void add(float w, float ex)
-    {
-        wmin = fminf(wmin, w);
-        wmax = fmaxf(wmax, w);
-        excess = fmaxf(excess, ex);
-    }
-    __device__ void flush(Counters *c) const
-    {
-        float a = wmin, b = wmax, e = excess;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a = fminf(a, __shfl_xor_sync(0xffffffffu, a, o));
-            b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, o));
-            e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicMin(&c->omega_min_bits, __float_as_uint(a));
-            atomicMax(&c->omega_max_bits, __float_as_uint(b));
-            if (e > 0.0f) atomicMax(&c->excess_max_bits, __float_as_uint(e));
-        }
-    }
-};
-
 // One relaxation of one cell (eq. relaxationDiscretizationOmega), in place.
-// With DIAG the cell's entropy change is checked (entropy_excess); the relaxed
-// values do not depend on DIAG.
-template <class Sys, class R, int OM, bool DIAG>
-__device__ __forceinline__ void relax_cell(const ParamsR<R> &P, R *f, int kind, bool &fallback, bool &increase,
-                                           R &omega_used, float &excess)
+// rec: this relaxation's record (diagnostics, see Params::rec) or null; the
+// record only stores values the relaxation computes anyway.
+template <class Sys, class R, int OM>
+__device__ __forceinline__ void relax_cell(const ParamsR<R> &P, R *f, int kind, bool &fallback, R *rec)
 {
     constexpr int Q = Sys::Q, M = Sys::M;
+    const int64_t fs = (int64_t)P.rec_stages * P.rec_cells;  // distance between the fields of a record
     R u[M], feq[Q * M];
     moments_target<Sys, R>(P, f, u, feq);
     fallback = false;
-    increase = false;
-    excess = 0.0f;
     if (kind == KIND_PROJECT) {  // R_1: projection on the equilibrium (Section 6.1)
-        omega_used = R(1);
+        if (rec) rec[(M + Q * M) * fs] = R(1);
 #pragma unroll
         for (int i = 0; i < Q * M; ++i) f[i] = feq[i];
         return;
@@ -242,26 +181,40 @@ __device__ __forceinline__ void relax_cell(const ParamsR<R> &P, R *f, int kind, 
     R delta[Q * M];
 #pragma unroll
     for (int i = 0; i < Q * M; ++i) delta[i] = feq[i] - f[i];
+    if (rec) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) rec[m * fs] = u[m];
+#pragma unroll
+        for (int i = 0; i < Q * M; ++i) rec[(M + i) * fs] = delta[i];
+    }
     R w = P.omega;
     if constexpr (OM != OM_FIXED && !Sys::LINEAR) {
         typename Sys::template Ctx<R> cx;
         Sys::template prepare<R>(P, u, delta, cx);
         w = entropic_omega<Sys, R>(P, cx, fallback);
         if constexpr (OM == OM_MIXED) w = mixed_omega<Sys, R>(P, u, delta, w, fallback);
-        if constexpr (DIAG) {
-            excess = entropy_excess<Sys, R>(P, u, delta, w);
-            increase = entropy_increase<R, OM>(excess);
-        }
     } else if constexpr (OM != OM_FIXED) {
         w = R(2);  // quadratic kinetic entropies: omega* = 2 exactly (Proposition 2)
     }
-    omega_used = w;
+    if (rec) rec[(M + Q * M) * fs] = w;
 #pragma unroll
     for (int i = 0; i < Q * M; ++i) f[i] += w * delta[i];
 }
 
+// Kernels that record their relaxations for the diagnostics (entropic omega,
+// nonlinear system): the record of stage st of a launch at cell c, or null.
+template <class Sys, int OM> constexpr bool checked() { return OM != OM_FIXED && !Sys::LINEAR; }
+
+template <class Sys, class R, int OM>
+__device__ __forceinline__ R *record_of(const ParamsR<R> &P, int st, int64_t cell, bool on)
+{
+    if constexpr (checked<Sys, OM>())
+        return (P.rec && on) ? P.rec + (int64_t)st * P.rec_cells + cell : nullptr;
+    return nullptr;
+}
+
 // Fused stage: pull-shift by sh (transport, eq. transportPhase) then relax.
-template <class Sys, int DIM, class R, int OM, bool DIAG>
+template <class Sys, int DIM, class R, int OM>
 __global__ void __launch_bounds__(kBlock) k_stage(StageArgs<R> a, ParamsR<R> P)
 {
     constexpr int Q = Sys::Q, M = Sys::M;
@@ -269,8 +222,7 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageArgs<R> a, ParamsR<R> P)
     const int64_t y = blockIdx.y;
     const bool valid = x < a.nx;
     R f[Q * M];
-    bool fb = false, inc = false;
-    DiagAcc acc;
+    bool fb = false;
     if (valid) {
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
@@ -278,19 +230,12 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageArgs<R> a, ParamsR<R> P)
 #pragma unroll
             for (int m = 0; m < M; ++m) f[k * M + m] = a.fin[(int64_t)(k * M + m) * a.ncell + s];
         }
-        R w;
-        float ex;
-        relax_cell<Sys, R, OM, DIAG>(P, f, a.kind, fb, inc, w, ex);
-        if constexpr (DIAG) acc.add(float(w), ex);
         const int64_t o = y * a.nx + x;
+        relax_cell<Sys, R, OM>(P, f, a.kind, fb, record_of<Sys, R, OM>(P, 0, o, true));
 #pragma unroll
         for (int i = 0; i < Q * M; ++i) a.fout[(int64_t)i * a.ncell + o] = f[i];
     }
-    if constexpr (OM != OM_FIXED && !Sys::LINEAR) warp_count(valid && fb, &a.cnt->fallbacks);
-    if constexpr (DIAG) {
-        warp_count(valid && inc, &a.cnt->entropy_increases);
-        acc.flush(a.cnt);
-    }
+    if constexpr (checked<Sys, OM>()) warp_count(valid && fb, &a.cnt->fallbacks);
 }
 
 // ---------------------------------------------------------------------------
@@ -327,7 +272,7 @@ template <class R> struct BulkArgs {
     Counters *cnt;
 };
 
-template <class Sys, class R, int OM, bool DIAG>
+template <class Sys, class R, int OM>
 __global__ void __launch_bounds__(kRowThreads) k_stage_bulk(BulkArgs<R> a, ParamsR<R> P)
 {
     constexpr int Q = Sys::Q, M = Sys::M, NP = Q * M;
@@ -403,27 +348,21 @@ __global__ void __launch_bounds__(kRowThreads) k_stage_bulk(BulkArgs<R> a, Param
         if (threadIdx.x == 0) atomicAdd(&a.cnt->copy_timeouts, 1ull);
         return;
     }
-    DiagAcc acc;
     for (int j0 = 0; j0 < kRowTile; j0 += kRowThreads) {  // same trip count for every thread
         const int j = j0 + threadIdx.x;
         const bool valid = j < T;
-        bool fb = false, inc = false;
+        bool fb = false;
         if (valid) {
             R f[NP];
 #pragma unroll
             for (int p = 0; p < NP; ++p) f[p] = sm[(int64_t)p * a.slot + s_off[p] + j];
-            R w;
-            float ex;
-            relax_cell<Sys, R, OM, DIAG>(P, f, a.kind, fb, inc, w, ex);
-            if constexpr (DIAG) acc.add(float(w), ex);
             const int64_t o = y * a.nx + x0 + j;
+            relax_cell<Sys, R, OM>(P, f, a.kind, fb, record_of<Sys, R, OM>(P, 0, o, true));
 #pragma unroll
             for (int p = 0; p < NP; ++p) a.fout[(int64_t)p * a.ncell + o] = f[p];
         }
-        if constexpr (OM != OM_FIXED && !Sys::LINEAR) warp_count(fb, &a.cnt->fallbacks);
-        if constexpr (DIAG) warp_count(inc, &a.cnt->entropy_increases);
+        if constexpr (checked<Sys, OM>()) warp_count(fb, &a.cnt->fallbacks);
     }
-    if constexpr (DIAG) acc.flush(a.cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -452,8 +391,12 @@ template <class R> struct FusedArgs {
     int nrec;
 };
 
-template <class Sys, class R, int OM, bool RECORD = false, bool DIAG = false>
-__global__ void __launch_bounds__(kFusedBlock, sizeof(R) == 4 ? 4 : 2)
+// Four resident blocks per SM (64 registers a thread) for the FP32 relaxation; two (128) where
+// an FP64 evaluation joins it (FP64 storage, the mixed mode).
+template <class R, int OM> constexpr int step1d_min_blocks() { return (sizeof(R) == 4 && OM != OM_MIXED) ? 4 : 2; }
+
+template <class Sys, class R, int OM, bool RECORD = false>
+__global__ void __launch_bounds__(kFusedBlock, step1d_min_blocks<R, OM>())
     k_step1d(FusedArgs<R> a, StageList sl, ParamsR<R> P)
 {
     constexpr int Q = Sys::Q, M = Sys::M, NP = Q * M;
@@ -475,7 +418,6 @@ __global__ void __launch_bounds__(kFusedBlock, sizeof(R) == 4 ? 4 : 2)
 #pragma unroll
     for (int k = 0; k < Q; ++k) off[k] = 0;
     int moved = 0;  // sum of |shift| over the stages so far
-    DiagAcc acc;
     for (int st = 0; st < sl.n; ++st) {
         const int s = sl.shift[st], kind = sl.kind[st];
 #pragma unroll
@@ -489,7 +431,7 @@ __global__ void __launch_bounds__(kFusedBlock, sizeof(R) == 4 ? 4 : 2)
         for (int jj = threadIdx.x; jj < jend; jj += blockDim.x) {
             const int j = jlo + jj;
             const bool valid = jj < cnt;
-            bool fb = false, inc = false;
+            bool fb = false;
             if (valid) {
                 int slot[Q];
 #pragma unroll
@@ -503,22 +445,16 @@ __global__ void __launch_bounds__(kFusedBlock, sizeof(R) == 4 ? 4 : 2)
                 for (int k = 0; k < Q; ++k)
 #pragma unroll
                     for (int m = 0; m < M; ++m) f[k * M + m] = sm[(k * M + m) * W + slot[k]];
-                R w;
-                float ex;
-                relax_cell<Sys, R, OM, DIAG>(P, f, kind, fb, inc, w, ex);
-                // only cells of the final tile count towards the counters (each cell-stage once)
+                // only cells of the final tile count and record (each cell-stage once)
                 const bool in_tile = j >= H && j < H + T;
+                relax_cell<Sys, R, OM>(P, f, kind, fb, record_of<Sys, R, OM>(P, st, x0 + j - H, in_tile));
                 fb = fb && in_tile;
-                inc = inc && in_tile;
-                if constexpr (DIAG)
-                    if (in_tile) acc.add(float(w), ex);
 #pragma unroll
                 for (int k = 0; k < Q; ++k)
 #pragma unroll
                     for (int m = 0; m < M; ++m) sm[(k * M + m) * W + slot[k]] = f[k * M + m];
             }
-            if constexpr (OM != OM_FIXED && !Sys::LINEAR) warp_count(fb, &a.cnt->fallbacks);
-            if constexpr (DIAG) warp_count(inc, &a.cnt->entropy_increases);
+            if constexpr (checked<Sys, OM>()) warp_count(fb, &a.cnt->fallbacks);
         }
         __syncthreads();
         if constexpr (RECORD) {
@@ -537,7 +473,6 @@ __global__ void __launch_bounds__(kFusedBlock, sizeof(R) == 4 ? 4 : 2)
             }
         }
     }
-    if constexpr (DIAG) acc.flush(a.cnt);
     // write the exact tile
     for (int j = threadIdx.x; j < T; j += blockDim.x) {
 #pragma unroll
@@ -731,13 +666,12 @@ template <class R> struct BatchArgs {
     Counters *cnt;
 };
 
-template <class Sys, class R, int OM, bool DIAG>
+template <class Sys, class R, int OM>
 __global__ void __launch_bounds__(kBlock) k_batch_step(BatchArgs<R> a, StageList sl, ParamsR<R> P)
 {
     constexpr int Q = Sys::Q, M = Sys::M;
     cg::grid_group grid = cg::this_grid();
     int side = a.side;
-    DiagAcc acc;
     for (int st = 0; st < sl.n; ++st) {
         const R *__restrict__ fin = a.pool[side];
         R *__restrict__ fout = a.pool[side ^ 1];
@@ -757,7 +691,7 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchArgs<R> a, StageList
             }
             for (int j = threadIdx.x; j < ((w.nx + 31) / 32) * 32; j += blockDim.x) {
                 const bool valid = j < w.nx;
-                bool fb = false, inc = false;
+                bool fb = false;
                 if (valid) {
                     const int64_t x = w.x0 + j, y = w.y;
                     R f[Q * M];
@@ -767,22 +701,17 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchArgs<R> a, StageList
 #pragma unroll
                         for (int m = 0; m < M; ++m) f[k * M + m] = fi[(int64_t)(k * M + m) * ncell + src];
                     }
-                    R wv;
-                    float ex;
-                    relax_cell<Sys, R, OM, DIAG>(P, f, kind, fb, inc, wv, ex);
-                    if constexpr (DIAG) acc.add(float(wv), ex);
                     const int64_t o = y * I.nx + x;
+                    relax_cell<Sys, R, OM>(P, f, kind, fb, record_of<Sys, R, OM>(P, st, I.cell0 + o, true));
 #pragma unroll
                     for (int i = 0; i < Q * M; ++i) fo[(int64_t)i * ncell + o] = f[i];
                 }
-                if constexpr (OM != OM_FIXED && !Sys::LINEAR) warp_count(fb, &a.cnt->fallbacks);
-                if constexpr (DIAG) warp_count(inc, &a.cnt->entropy_increases);
+                if constexpr (checked<Sys, OM>()) warp_count(fb, &a.cnt->fallbacks);
             }
         }
         side ^= 1;
         grid.sync();
     }
-    if constexpr (DIAG) acc.flush(a.cnt);
 }
 
 // f_k = f^eq_k(u0) (Section 3.1) with the domain check of Section 1.2.

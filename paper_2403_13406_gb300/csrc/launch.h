@@ -36,10 +36,34 @@ struct FusedLaunch {
 };
 
 // temporally blocked 1D step (several stages in shared memory); 1D families only
-cudaError_t launch_fused1d(int family, bool fp64, int om, bool diag, const FusedLaunch &L);
+cudaError_t launch_fused1d(int family, bool fp64, int om, const FusedLaunch &L);
+
+struct Step2dLaunch {
+    const void *fin;
+    void *fout;
+    int64_t nx, ny, ncell;
+    StageList sl;  // the stages of this launch (halo = sum |shift|)
+    Plan2d plan;   // from plan_step2d
+    Counters *cnt;
+    Params P;
+    cudaStream_t stream;
+};
+
+// Plan of one launch of the temporally blocked 2D kernel for the stages sl on an
+// nx x ny grid with `planes` planes of `elem`-byte values on `sms` SMs; false if
+// the stages do not fit (rows not on 16-byte boundaries, ring or window too large).
+bool plan_step2d(int64_t nx, int64_t ny, int planes, int elem, int sms, const StageList &sl, Plan2d &out);
+// several fused stages of a 2D lattice in one launch (plan from plan_step2d)
+cudaError_t launch_step2d(int family, bool fp64, int om, const Step2dLaunch &L);
+// SMs of the current device (cached per device)
+int device_sms();
 
 // fused pull-shift + relaxation stage
-cudaError_t launch_stage(int family, bool fp64, int om, bool diag, const StageLaunch &L);
+cudaError_t launch_stage(int family, bool fp64, int om, const StageLaunch &L);
+// Diagnostics: fields of one relaxation record (M moments, q M deviations, omega) and the
+// per-cell check of the records the previous launch wrote (P.rec, rec_stages, rec_cells)
+inline int record_fields(int q, int M) { return M + q * M + 1; }
+cudaError_t launch_check(int family, bool fp64, int om, const Params &P, Counters *cnt, cudaStream_t st);
 // f = f^eq(u0) with the domain check
 cudaError_t launch_init_eq(int family, bool fp64, const double *u0, void *f, int64_t ncell, const Params &P,
                            Counters *cnt, cudaStream_t st);
@@ -93,9 +117,9 @@ struct BatchLaunch {
 };
 
 // one composite step of every instance of a 2D batch (cooperative, grid.sync between stages)
-cudaError_t launch_batch_step(int family, bool fp64, int om, bool diag, const BatchLaunch &L);
+cudaError_t launch_batch_step(int family, bool fp64, int om, const BatchLaunch &L);
 // resident blocks per SM of that kernel (0 if the family has no batched kernel)
-int batch_blocks_per_sm(int family, bool fp64, int om, bool diag);
+int batch_blocks_per_sm(int family, bool fp64, int om);
 
 int totals_blocks();
 

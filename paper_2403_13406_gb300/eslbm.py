@@ -49,7 +49,7 @@ class Sizes(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int64), ("M", ctypes.c_int64), ("planes", ctypes.c_int64),
                 ("ncell", ctypes.c_int64), ("state_bytes", ctypes.c_uint64),
                 ("workspace_bytes", ctypes.c_uint64), ("stages_per_step", ctypes.c_int64),
-                ("step_cells", ctypes.c_int64)]
+                ("step_cells", ctypes.c_int64), ("launches_per_step", ctypes.c_double)]
 
 
 class Diagnostics(ctypes.Structure):
@@ -137,7 +137,8 @@ def make_config(dim, system, nx, ny=1, V=1.0, precision="fp32", omega_mode="fixe
                 a=(0.0, 0.0), c=(1.0, 1.0), g=1.0, gamma=1.4, t_max=3.0, kappa=1, diagnostics=False, u_ref=None,
                 blocking=True):
     """Configuration of one lattice; u_ref (conserved values) selects the shifted storage; precision is
-    "fp32", "fp64" or "fp32_mixed"; blocking=False runs one launch per fused stage."""
+    "fp32", "fp64" or "fp32_mixed"; blocking=False runs one launch per fused stage, an int n >= 2 at
+    most n stages per temporally blocked 2D launch."""
     cfg = Config()
     cfg.dim = int(dim)
     cfg.system = SYSTEMS[system] if isinstance(system, str) else int(system)
@@ -156,7 +157,12 @@ def make_config(dim, system, nx, ny=1, V=1.0, precision="fp32", omega_mode="fixe
     cfg.t_max = float(t_max)
     cfg.diagnostics = 1 if diagnostics else 0
     cfg.shifted = 0 if u_ref is None else 1
-    cfg.blocking = BLOCKING_AUTO if blocking else BLOCKING_OFF
+    if blocking is True or blocking is None:
+        cfg.blocking = BLOCKING_AUTO
+    elif blocking is False:
+        cfg.blocking = BLOCKING_OFF
+    else:
+        cfg.blocking = int(blocking)  # at most this many stages per 2D launch
     if u_ref is not None:
         for i, v in enumerate(u_ref):
             cfg.u_ref[i] = float(v)

@@ -94,16 +94,19 @@ def test_shifted_reference_is_accepted(L):
 
 
 def test_mixed_precision_and_blocking_fields(L):
-    """FP32_MIXED stores FP32 (same buffer sizes as FP32); blocking takes AUTO or OFF only."""
+    """FP32_MIXED stores FP32 (same buffer sizes as FP32); blocking takes AUTO (0), OFF (1) or a largest
+    group of stages per 2D launch (2..32)."""
     a = eslbm.query(q(system="sw", V=4.0, g=9.81, precision="fp32", omega_mode="entropic"))
     b = eslbm.query(q(system="sw", V=4.0, g=9.81, precision="fp32_mixed", omega_mode="entropic"))
     assert a.state_bytes == b.state_bytes == 4 * 256 * 4
     assert eslbm.query(q(blocking=False)).planes == 2
-    bad = q()
-    bad.blocking = 2
-    with pytest.raises(eslbm.EslbmError) as e:
-        eslbm.query(bad)
-    assert e.value.status == eslbm.ERR_ARG
+    assert eslbm.query(q(blocking=6)).planes == 2
+    for v in (-1, 33):
+        bad = q()
+        bad.blocking = v
+        with pytest.raises(eslbm.EslbmError) as e:
+            eslbm.query(bad)
+        assert e.value.status == eslbm.ERR_ARG
 
 
 def test_structs_match_header(L, tmp_path):

@@ -1,0 +1,166 @@
+"""The temporally blocked 2D kernel (several fused stages per launch from a ring of rows in
+shared memory) against one launch per stage and against the FP64 oracle.
+
+Runs with blocking on take the blocked kernel wherever rows start on 16-byte boundaries (nx a
+multiple of 4 in FP32, 2 in FP64).  The per-cell arithmetic is the relaxation of the per-stage
+kernels; only the transport (index arithmetic in shared memory instead of pulled loads) and the
+number of launches differ, so the two agree to rounding (bitwise where the compiler contracts the
+products alike).  Sizes cover several strips and segments with ragged last ones, windows wider
+than the grid, and every group size of a step.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2403_13406_gb300 import eslbm, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def rel_max(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+CASES = {
+    "burgers": ("burgers", 1032, 6, dict(V=3.0, c=(1.0, 0.6)), lambda nx, ny: inputs.burgers_2d(nx, ny, seed=8)),
+    "burgers_mid": ("burgers", 256, 200, dict(V=3.0, c=(1.0, 1.0)), lambda nx, ny: inputs.burgers_2d(nx, ny, seed=3)),
+    "sw": ("sw", 1032, 3, dict(V=8.0, g=9.81), lambda nx, ny: inputs.sw_random_2d(nx, ny, seed=9, h_amp=0.03)),
+    "sw_mid": ("sw", 200, 132, dict(V=8.0, g=9.81), lambda nx, ny: inputs.sw_random_2d(nx, ny, seed=2, h_amp=0.1)),
+    "linear": ("linear", 300, 7, dict(V=1.0, a=(0.2, -0.15)), lambda nx, ny: inputs.linear_sine_2d(nx, ny)),
+    "linear_narrow": ("linear", 4, 9, dict(V=1.0, a=(0.2, -0.15)), lambda nx, ny: inputs.linear_sine_2d(nx, ny)),
+    "euler": ("euler", 40, 36, dict(V=8.0, gamma=1.4), lambda nx, ny: inputs.euler_vortex_2d(nx, ny)),
+    "euler_mid": ("euler", 416, 300, dict(V=8.0, gamma=1.4), lambda nx, ny: inputs.euler_vortex_2d(nx, ny)),
+}
+
+
+def run(name, mode, precision, steps, scheme="I", blocking=True, diagnostics=False):
+    system, nx, ny, kw, init = CASES[name]
+    cfg = eslbm.make_config(2, system, nx, ny, precision=precision, omega_mode=mode, scheme=scheme,
+                            blocking=blocking, diagnostics=diagnostics, **kw)
+    sim = eslbm.Simulation(cfg)
+    sim.init_equilibrium(init(nx, ny))
+    sim.step(steps)
+    f = sim.distributions(host=True)
+    d = sim.diagnostics()
+    sim.close()
+    return f, d
+
+
+VARIANTS = [(n, "fixed", p) for n in CASES for p in ("fp32", "fp64")] + \
+           [(n, "entropic", p) for n in ("burgers", "burgers_mid", "sw", "sw_mid") for p in ("fp32", "fp64", "fp32_mixed")]
+
+
+@pytest.mark.parametrize("name,mode,precision", VARIANTS)
+def test_blocked_matches_per_stage(name, mode, precision):
+    a, da = run(name, mode, precision, 3, blocking=True)
+    b, db = run(name, mode, precision, 3, blocking=False)
+    if precision == "fp64":
+        assert rel_max(a, b) <= 1e-13
+    elif mode == "fixed":
+        assert rel_max(a, b) <= 1e-6
+    else:
+        # the root-finder is inlined into two kernels whose FMA contraction may differ: 3 steps of
+        # independently rounded FP32 paths are held to the FP32 bar
+        assert rel_l2(a, b) <= 1e-5
+    assert da["fallbacks"] == db["fallbacks"]
+
+
+@pytest.mark.parametrize("group", [2, 3, 4, 5, 6, 9, 18])
+def test_every_group_size(group):
+    """The stages of a step split into launches of at most `group` stages: the same result."""
+    ref, _ = run("euler_mid", "fixed", "fp64", 2, blocking=False)
+    got, _ = run("euler_mid", "fixed", "fp64", 2, blocking=group)
+    assert rel_max(got, ref) <= 1e-13
+
+
+@pytest.mark.parametrize("scheme", ["II", "III", "IV", "B", "plain"])
+def test_scheme_variants_blocked(scheme):
+    """Projections R_1 (a stage without transport) and the short schemes through the blocked kernel,
+    against the FP64 oracle."""
+    system, nx, ny, kw, init = CASES["euler"]
+    u0 = init(nx, ny)
+    m = O.Model(2, system, nx, ny, **kw)
+    ref = O.init_equilibrium(m, u0)
+    O.composite_steps(m, ref, 3, scheme=scheme)
+    got, _ = run("euler", "fixed", "fp64", 3, scheme=scheme)
+    assert rel_max(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("name,mode", [("burgers_mid", "entropic"), ("sw_mid", "entropic"), ("euler_mid", "fixed")])
+def test_blocked_matches_oracle_fp64(name, mode):
+    system, nx, ny, kw, init = CASES[name]
+    u0 = init(nx, ny)
+    m = O.Model(2, system, nx, ny, omega_mode=mode, **kw)
+    ref = O.init_equilibrium(m, u0)
+    O.composite_steps(m, ref, 2)
+    got, d = run(name, mode, "fp64", 2)
+    assert rel_max(got, ref) <= 1e-12
+    assert d["fallbacks"] == 0
+
+
+def test_full_size_euler_vortex_sampled():
+    """Euler 8192^2 isentropic vortex (V = 8, omega = 2, scheme I, FP32) through the blocked kernel:
+    one composite step checked on sampled periodic windows of 75 x 75 cells by the FP64 oracle (a
+    step's dependence cone has half-width sum |s| = 36), and the conserved totals kept."""
+    n, half = 8192, 37
+    kw = dict(V=8.0, gamma=1.4)
+    cfg = eslbm.make_config(2, "euler", n, n, precision="fp32", omega_mode="fixed", **kw)
+    sim = eslbm.Simulation(cfg)
+    sim.init_equilibrium(inputs.euler_vortex_2d(n, n))
+    t0 = sim.totals()
+    sim.step(2)
+    f_in = sim.distributions(host=False)
+    samples = [(0, 0), (n - 1, 5), (4100, 4090), (777, 8191), (6000, 1234)]
+    wins = []
+    for py, px in samples:
+        iy = torch.as_tensor((np.arange(-half, half + 1) + py) % n, device=f_in.device)
+        ix = torch.as_tensor((np.arange(-half, half + 1) + px) % n, device=f_in.device)
+        wins.append(f_in[:, iy][:, :, ix].cpu().numpy())
+    del f_in
+    sim.step(1)
+    f_out = sim.distributions(host=False)
+    outs = [f_out[:, py, px].cpu().numpy() for py, px in samples]
+    del f_out
+    t1 = sim.totals()
+    sim.close()
+    for win, got in zip(wins, outs):
+        win = np.ascontiguousarray(win)
+        mw = O.Model(2, "euler", 2 * half + 1, 2 * half + 1, **kw)
+        O.composite_steps(mw, win, 1)
+        ref = win[:, half, half]
+        assert np.abs(got - ref).max() / np.abs(ref).max() <= 5e-6
+    for m in range(4):
+        assert abs(t1[2 + m] - t0[2 + m]) <= 1e-6 * max(abs(t0[2]), abs(t0[5]))
+
+
+def test_euler_random_riemann_500_steps():
+    """Euler 4096^2 seeded random-interface Riemann data (four constant states, V = 8), scheme III with
+    omega = 2 (the paper's Euler setting), 500 composite steps through the blocked kernel: the state
+    stays finite with positive density and pressure, and mass, momentum and energy are conserved to
+    the FP32 rounding of the reductions' inputs."""
+    n = 4096
+    cfg = eslbm.make_config(2, "euler", n, n, V=8.0, gamma=1.4, precision="fp32", omega_mode="fixed",
+                            scheme="III")
+    sim = eslbm.Simulation(cfg)
+    sim.use_graph(True)
+    sim.init_equilibrium(inputs.euler_riemann_2d(n, n))
+    t0 = sim.totals()
+    sim.step(500)
+    u = sim.moments(host=False)
+    t1 = sim.totals()
+    sim.close()
+    assert bool(torch.isfinite(u).all())
+    rho = u[0]
+    p = 0.4 * (u[3] - 0.5 * (u[1] ** 2 + u[2] ** 2) / rho)
+    assert float(rho.min()) > 0 and float(p.min()) > 0
+    scale = max(abs(t0[2]), abs(t0[5]))
+    for m in range(4):
+        assert abs(t1[2 + m] - t0[2 + m]) <= 2e-6 * scale

@@ -4,8 +4,9 @@ With diagnostics on, every entropic relaxation evaluates F(omega - 1) = B(omega 
 FP64 (the change of the cell's microscopic entropy) and counts the cells above the rounding level
 of the arithmetic that chose omega.  The check reads what the relaxation computed and writes
 nothing back: the distributions are bit for bit those of the same kernel without it.  Cases cover
-the temporally blocked 1D kernel, the staged 2D stage kernel (rows on 16-byte boundaries) and the
-batched cooperative kernel, in FP32, FP64 and FP32 with the entropy difference in FP64.
+the temporally blocked 1D and 2D kernels, the per-stage kernels (the staged 2D stage kernel for rows
+on 16-byte boundaries) and the batched cooperative kernel, in FP32, FP64 and FP32 with the entropy
+difference in FP64.
 """
 import numpy as np
 import pytest
@@ -32,9 +33,10 @@ CASES = {
 }
 
 
-def run(name, precision, diag, steps=6):
+def run(name, precision, diag, steps=6, blocking=True):
     dim, system, nx, ny, kw, init = CASES[name]
-    cfg = eslbm.make_config(dim, system, nx, ny, precision=precision, omega_mode="entropic", diagnostics=diag, **kw)
+    cfg = eslbm.make_config(dim, system, nx, ny, precision=precision, omega_mode="entropic", diagnostics=diag,
+                            blocking=blocking, **kw)
     sim = eslbm.Simulation(cfg)
     sim.init_equilibrium(init())
     sim.step(steps)
@@ -46,9 +48,12 @@ def run(name, precision, diag, steps=6):
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("precision", ["fp32", "fp64", "fp32_mixed"])
-def test_diagnostics_leave_results_unchanged(name, precision):
-    f0, d0 = run(name, precision, False)
-    f1, d1 = run(name, precision, True)
+@pytest.mark.parametrize("blocking", [True, False])
+def test_diagnostics_leave_results_unchanged(name, precision, blocking):
+    """blocking on: the 1D and 2D temporally blocked kernels; off: the per-stage kernels (2D rows on
+    16-byte boundaries: the bulk-copy staged stage kernel)."""
+    f0, d0 = run(name, precision, False, blocking=blocking)
+    f1, d1 = run(name, precision, True, blocking=blocking)
     assert np.array_equal(f0, f1)
     assert d0["fallbacks"] == d1["fallbacks"]
     assert d1["entropy_increases"] == 0

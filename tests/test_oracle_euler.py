@@ -75,3 +75,27 @@ def test_euler_vortex_fourth_order():
         ex = inputs.euler_vortex_2d(N, N, centre=(5 + n * dt, 5 + n * dt))
         errs.append(math.sqrt((10.0 / N) ** 2 * float(np.sum((u[0] - ex[0]) ** 2))))
     assert math.log2(errs[0] / errs[1]) > 4.0
+
+
+@pytest.mark.parametrize("system,kw,mode", [("euler", dict(V=8.0, gamma=1.4), "fixed"),
+                                            ("sw", dict(V=8.0, g=9.81), "entropic")])
+def test_openmp_build_is_the_same_arithmetic(system, kw, mode):
+    """The OpenMP build of the oracle (timed on all host cores as the CPU baseline) splits the cells of a
+    relaxation sweep and the planes of a transport over threads: the results are bit for bit those of
+    the single-threaded build, and so are the statistics."""
+    nx, ny = 48, 40
+    u0 = inputs.euler_vortex_2d(nx, ny) if system == "euler" else inputs.sw_random_2d(nx, ny, seed=3, h_amp=0.1)
+    out = []
+    try:
+        for omp in (False, True):
+            if not O.set_openmp(omp):
+                pytest.skip("no OpenMP in this compiler")
+            m = O.Model(2, system, nx, ny, omega_mode=mode, **kw)
+            f = O.init_equilibrium(m, u0)
+            st = O.Stats()
+            O.composite_steps(m, f, 1, stats=st)
+            out.append((f, st.as_dict()))
+    finally:
+        O.set_openmp(False)
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
