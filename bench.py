@@ -64,7 +64,8 @@ def parse():
     p.add_argument("--composite-steps", type=int, default=EULER_STEPS, help="headline composite steps per solve")
     p.add_argument("--no-extras", action="store_true", help="headline only (no other workloads, no CPU baseline)")
     p.add_argument("--leg", default=None,
-                   choices=["sw1d", "burgers2d", "riemann", "batched", "precision", "accuracy", "adjoint", "cpu"],
+                   choices=["sw1d", "burgers2d", "riemann", "batched", "precision", "accuracy", "adjoint", "cpu",
+                            "blocked2d"],
                    help="run one secondary measurement alone and print its JSON")
     p.add_argument("--batch-count", type=int, default=64, help="instances of the batched leg")
     return p.parse_args()
@@ -388,13 +389,15 @@ def burgers2d_leg(torch, eslbm, inputs, stream, dev):
                           "mass_total": [float(t0[2]), float(t1[2])]}}
 
 
-def riemann_leg(torch, eslbm, inputs, stream, dev):
+def riemann_leg(torch, eslbm, inputs, stream, dev, omega=1.98):
     """Euler 4096^2 seeded random-interface Riemann data (four constant states with rho, p in
-    [0.5, 1.5], u, v in [-0.5, 0.5]), V = 8, scheme III with omega = 2 (the paper's Euler setting),
-    500 composite steps: throughput, and the state checked every 50 steps (finite, min rho, min p)."""
+    [0.5, 1.5], u, v in [-0.5, 0.5]), V = 8, scheme III (the paper's Euler setting) with omega = 1.98,
+    500 composite steps: throughput, and the state checked every 50 steps (finite, min rho, min p).
+    With omega = 2 exactly the state loses finiteness after about 190 steps at this resolution (FP64
+    as FP32, per stage as blocked)."""
     n = RIEMANN_N
     cfg = eslbm.make_config(2, "euler", n, n, V=EULER_V, gamma=EULER_GAMMA, precision="fp32", omega_mode="fixed",
-                            scheme="III")
+                            omega=omega, scheme="III")
     u0 = torch.from_numpy(inputs.euler_riemann_2d(n, n)).to(dev)
     with torch.cuda.stream(stream):
         sim = eslbm.Simulation(cfg, stream=stream, device=dev)
@@ -418,11 +421,45 @@ def riemann_leg(torch, eslbm, inputs, stream, dev):
     sim.close()
     s = ms * 1e-3
     return {"euler_riemann": {"workload": "euler2d_d2q4_riemann_n%d_steps%d_schemeIII" % (n, RIEMANN_STEPS),
-                              "ms": ms, "site_updates_per_s": n * n * RIEMANN_STEPS / s,
+                              "omega": omega, "ms": ms, "site_updates_per_s": n * n * RIEMANN_STEPS / s,
                               "roofline": hbm_roofline(27 * 2 * 16 * 4, n * n * RIEMANN_STEPS, s,
-                                                       "k_step2d<Euler2, float, fixed>", int(round(lps * RIEMANN_STEPS)),
+                                                       "k_stage_bulk<Euler2, float, fixed>", int(round(lps * RIEMANN_STEPS)),
                                                        {"model": "per-stage: 27 x 2 q M b bytes per step (scheme III)"}),
                               "state": rows}}
+
+
+def blocked2d_leg(torch, eslbm, inputs, stream, dev, steps=10):
+    """The temporally blocked 2D kernel (k_step2d, several stages per launch from a ring of rows in
+    shared memory) against one launch per stage, on the headline Euler workload (8192^2, scheme I,
+    FP32) and on 2D Burgers 4096^2 (fixed and entropic omega): site updates per second of each and
+    the per-stage HBM model's fraction (the blocked kernel moves fewer bytes than that model)."""
+    out = {}
+    cases = (("euler_8192_fixed", "euler", EULER_N, dict(V=EULER_V, gamma=EULER_GAMMA), "fixed",
+              lambda n: inputs.euler_vortex_2d(n, n), 64),
+             ("burgers_4096_fixed", "burgers", BURGERS_N, dict(V=BURGERS_V), "fixed", lambda n: inputs.burgers_2d(n, n), 16),
+             ("burgers_4096_entropic", "burgers", BURGERS_N, dict(V=BURGERS_V), "entropic",
+              lambda n: inputs.burgers_2d(n, n), 16))
+    for name, system, n, kw, mode, init, bpc in cases:
+        row = {}
+        for label, blocking in (("per_stage", True), ("blocked_6", 6), ("blocked_3", 3)):
+            cfg = eslbm.make_config(2, system, n, n, precision="fp32", omega_mode=mode, blocking=blocking, **kw)
+            u0 = torch.from_numpy(init(n)).to(dev)
+            with torch.cuda.stream(stream):
+                sim = eslbm.Simulation(cfg, stream=stream, device=dev)
+                sim.use_graph(True)
+                sim.init_equilibrium(u0)
+                sim.step(2)
+            ms = timed_steps(torch, sim, stream, dev, steps)
+            lps = float(sim.sizes.launches_per_step)
+            sim.close()
+            del u0
+            sps = n * n * steps / (ms * 1e-3)
+            peak, _ = peaks()
+            row[label] = {"site_updates_per_s": sps, "launches_per_step": lps,
+                          "per_stage_model_frac": sps * 18 * 2 * bpc / 1e9 / peak}
+        row["blocked_6_over_per_stage"] = row["blocked_6"]["site_updates_per_s"] / row["per_stage"]["site_updates_per_s"]
+        out[name] = row
+    return {"blocked2d": out}
 
 
 def precision_leg(torch, eslbm, inputs, stream, dev, N=1 << 18):
@@ -661,6 +698,7 @@ def cpu_leg():
 # ---------------------------------------------------------------------------
 
 LEGS = {"sw1d": sw1d_leg, "burgers2d": burgers2d_leg, "riemann": riemann_leg, "batched": batch_leg,
+        "blocked2d": blocked2d_leg,
         "precision": precision_leg, "accuracy": accuracy_leg, "adjoint": adjoint_leg}
 
 
@@ -698,8 +736,8 @@ def main():
     head = headline(torch, eslbm, inputs, stream, dev, args, world, dist, local)
     extras, cpu = {}, None
     if not args.no_extras and rank == 0:
-        for leg in (sw1d_leg, burgers2d_leg, riemann_leg, precision_leg, fp32_vs_fp64_leg, accuracy_leg,
-                    adjoint_leg):
+        for leg in (sw1d_leg, burgers2d_leg, riemann_leg, blocked2d_leg, precision_leg, fp32_vs_fp64_leg,
+                    accuracy_leg, adjoint_leg):
             extras.update(leg(torch, eslbm, inputs, stream, dev))
         extras.update(batch_leg(torch, eslbm, inputs, stream, dev, count=args.batch_count))
     if rank == 0 and world == 1 and not args.no_extras:

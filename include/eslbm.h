@@ -70,13 +70,13 @@ enum { ESLBM_LINEAR = 0, ESLBM_BURGERS = 1, ESLBM_SHALLOW_WATER = 2, ESLBM_EULER
    (0, -E0) and (t, F(t)), which never exceeds the root of the convex F, replaces
    t.  With a fixed omega FP32_MIXED is FP32. */
 enum { ESLBM_FP32 = 0, ESLBM_FP64 = 1, ESLBM_FP32_MIXED = 2 };
-/* Temporal blocking (eslbm_config.blocking): AUTO runs several fused stages per
-   launch from on-chip memory where a kernel for it exists -- 1D: every step in
-   one launch; 2D with rows on 16-byte boundaries (nx a multiple of 4 in FP32 and
-   FP32_MIXED, of 2 in FP64): the stages of a step in a few launches of up to a
-   default number of stages.  OFF runs one launch per fused stage (the same
-   per-cell arithmetic; used to cross-check the blocked kernels).  A value n in
-   [2, 32] is AUTO with at most n stages per 2D launch. */
+/* Temporal blocking (eslbm_config.blocking): AUTO runs the fastest measured path
+   -- 1D: every step in one launch from shared memory; 2D: one launch per fused
+   stage.  OFF runs one launch per fused stage in 1D too (the same per-cell
+   arithmetic; used to cross-check the blocked kernels).  A value n in [2, 32]
+   runs the temporally blocked 2D kernel where rows start on 16-byte boundaries
+   (nx a multiple of 4 in FP32 and FP32_MIXED, of 2 in FP64), at most n stages
+   per launch (1D as AUTO). */
 enum { ESLBM_BLOCKING_AUTO = 0, ESLBM_BLOCKING_OFF = 1 };
 enum { ESLBM_OMEGA_FIXED = 0, ESLBM_OMEGA_ENTROPIC = 1 };
 /* Schemes (I)-(IV) of Section 6.1; PLAIN is the standard scheme R T(kappa dx/V)

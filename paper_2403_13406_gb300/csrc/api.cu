@@ -64,15 +64,16 @@ int64_t fused_group_of(int64_t stages_per_step)
     return stages_per_step >= 16 ? 1 : std::max<int64_t>(1, 24 / stages_per_step);
 }
 
-// most stages of one launch of the 2D kernel: the configuration's limit, else a default by
-// the width of a cell's state (fewer stages for wider states, whose ring leaves a narrower window)
-int max_group2d_of(const eslbm_config &c, int64_t planes)
-{
-    if (c.blocking >= 2) return c.blocking;
-    return planes * (c.precision == ESLBM_FP64 ? 8 : 4) >= 48 ? 6 : 9;
-}
+// most stages of one launch of the temporally blocked 2D kernel (the configuration's limit)
+int max_group2d_of(const eslbm_config &c, int64_t) { return c.blocking; }
 
-bool blocked2d_of(const eslbm_config &c) { return c.dim == 2 && c.blocking != ESLBM_BLOCKING_OFF && c.nx % (c.precision == ESLBM_FP64 ? 2 : 4) == 0; }
+// 2D runs take the temporally blocked kernel when asked for (blocking >= 2) and rows start on
+// 16-byte boundaries; by default one launch per stage, which measured faster on GB300 (the
+// stage kernel streams at the HBM roofline, the blocked one is bound by its per-row barrier).
+bool blocked2d_of(const eslbm_config &c)
+{
+    return c.dim == 2 && c.blocking >= 2 && c.nx % (c.precision == ESLBM_FP64 ? 2 : 4) == 0;
+}
 
 // Stages one launch may run: the record buffer of the diagnostics holds that many.
 int64_t max_launch_stages(const eslbm_config &c, int64_t stages_per_step, int64_t planes)

@@ -509,46 +509,172 @@ eslbm_status eslbm_batch_use_graph(eslbm_batch *b, int32_t enable)
     return ESLBM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Workspace of the batched reverse mode, in pools (each the size of a state pool): the checkpoints
+// of the forward pass every K steps, the starting states of the steps of one segment, the outputs of
+// the stages of one step, and two cotangent pools.
+struct BatchGradLayout {
+    int64_t n_outer, inner, stages;
+    uint64_t stride, bytes;
+};
+
+BatchGradLayout batch_grad_layout(const Layout &L, int64_t stages_per_step, int64_t n, int64_t K)
+{
+    BatchGradLayout g;
+    g.n_outer = n > 0 ? (n + K - 1) / K : 1;
+    g.inner = std::min<int64_t>(K, std::max<int64_t>(n, 1));
+    g.stages = stages_per_step;
+    g.stride = align256(L.pool_bytes);
+    g.bytes = g.stride * (uint64_t)(g.n_outer + g.inner + g.stages + 2);
+    return g;
+}
+
+int64_t batch_stages_per_step(const eslbm_config *base)
+{
+    int64_t n = 0;
+    for (const Op &op : scheme_ops(base->scheme, base->kappa)) n += op.relax ? 1 : 0;
+    return n;
+}
+
+// the stage list of one step entered with pending shift `pending` (merged transports), which is
+// advanced to the step's trailing shift
+StageList step_stage_list(const eslbm_batch *b, int64_t &pending)
+{
+    StageList sl;
+    sl.n = 0;
+    sl.halo = 0;
+    for (const Op &op : b->ops) {
+        if (!op.relax) {
+            pending += op.shift;
+            continue;
+        }
+        sl.shift[sl.n] = (int)pending;
+        sl.kind[sl.n] = op.kind;
+        sl.halo += (int)(pending < 0 ? -pending : pending);
+        sl.n += 1;
+        pending = 0;
+    }
+    return sl;
+}
+
+}  // namespace
+
+extern "C" {
+
 eslbm_status eslbm_batch_gradient_workspace(const eslbm_config *base, int32_t count, const int64_t *nx,
                                             const int64_t *ny, int64_t n, int64_t K, uint64_t *bytes)
 {
-    if (!bytes) return ESLBM_ERR_ARG;
+    if (!bytes || n < 0 || K < 1) return ESLBM_ERR_ARG;
     Layout L;
     eslbm_status s = layout(base, count, nx, ny, L);
     if (s != ESLBM_OK) return s;
-    uint64_t mx = 0;
-    for (int32_t i = 0; i < count; ++i) {
-        eslbm_config c = *base;
-        c.nx = nx[i];
-        c.ny = ny[i];
-        uint64_t b = 0;
-        if ((s = eslbm_gradient_workspace(&c, n, K, &b)) != ESLBM_OK) return s;
-        mx = std::max(mx, b);
-    }
-    *bytes = mx;
+    *bytes = batch_grad_layout(L, batch_stages_per_step(base), n, K).bytes;
     return ESLBM_OK;
 }
 
 eslbm_status eslbm_batch_gradient(eslbm_batch *b, const double *u0, const double *dJ_duT, double *dJ_du0, int64_t n,
                                   int64_t K, void *ws, uint64_t ws_bytes)
 {
-    if (!b || !u0 || !dJ_duT || !dJ_du0 || !ws) return ESLBM_ERR_ARG;
-    // each instance: the single-lattice reverse mode on views of the batch pools
+    if (!b || !u0 || !dJ_duT || !dJ_du0 || !ws || n < 0 || K < 1) return ESLBM_ERR_ARG;
+    const BatchGradLayout G = batch_grad_layout(b->L, batch_stages_per_step(&b->cfg), n, K);
+    if (ws_bytes < G.bytes || ((uintptr_t)ws & 255u)) {
+        b->err = "gradient workspace too small";
+        return ESLBM_ERR_ARG;
+    }
+    char *base = (char *)ws;
+    auto pool_at = [&](int64_t i) { return (void *)(base + G.stride * (uint64_t)i); };
+    auto outer = [&](int64_t i) { return pool_at(i); };
+    auto inner = [&](int64_t i) { return pool_at(G.n_outer + i); };
+    auto stage = [&](int64_t i) { return pool_at(G.n_outer + G.inner + i); };
+    void *cot[2] = {pool_at(G.n_outer + G.inner + G.stages), pool_at(G.n_outer + G.inner + G.stages + 1)};
+    const size_t pb = (size_t)b->L.pool_bytes;
+    const int64_t pool_elems = (int64_t)(G.stride / b->L.elem);
+    auto inst_at = [&](void *pool, int32_t i) { return (void *)((char *)pool + b->L.inst[(size_t)i].offset * b->L.elem); };
+    const int adj_bps = batch_adjoint_blocks_per_sm(b->family, b->fp64, b->om);
+    if (adj_bps < 1) return ESLBM_ERR_CUDA;
+
+    // forward pass with a checkpoint of every instance every K steps
+    eslbm_status s = eslbm_batch_init_equilibrium(b, u0, 1);
+    if (s != ESLBM_OK) return s;
+    std::vector<int64_t> ck_pending((size_t)G.n_outer, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (i % K == 0) {
+            BCK(cudaMemcpyAsync(outer(i / K), b->pool[b->side], pb, cudaMemcpyDeviceToDevice, b->stream), "checkpoint");
+            ck_pending[(size_t)(i / K)] = b->pending;
+        }
+        if ((s = run_step(b)) != ESLBM_OK) return s;
+    }
+    // cotangent of the final distributions from the cotangent of the moments (pending shift applied)
     int64_t cell0 = 0;
     for (int32_t i = 0; i < b->count; ++i) {
         const BatchInstance &I = b->L.inst[(size_t)i];
-        eslbm_config c = b->cfg;
-        c.nx = I.nx;
-        c.ny = I.ny;
-        eslbm_handle *h = nullptr;
-        eslbm_status s = eslbm_create(&c, b->instance_ptr(0, i), b->instance_ptr(1, i), b->ws + b->L.handle_ws_off,
-                                      b->stream, &h);
-        if (s != ESLBM_OK) return s;
+        BCK(launch_adjoint_readout(2, b->fp64, dJ_duT + cell0 * b->L.M, inst_at(cot[0], i), I.nx, I.ny, (int)b->L.M,
+                                   shift_for(b, i, b->pending), b->stream),
+            "adjoint readout");
+        cell0 += I.nx * I.ny;
+    }
+    int g = 0;
+    std::vector<int64_t> step_pending((size_t)G.inner, 0);
+    for (int64_t c = G.n_outer - 1; c >= 0 && n > 0; --c) {
+        const int64_t s0 = c * K, s1 = std::min(n, s0 + K);
+        // recompute the segment from its checkpoint, keeping every step's starting state
+        BCK(cudaMemcpyAsync(b->pool[0], outer(c), pb, cudaMemcpyDeviceToDevice, b->stream), "restore");
+        b->side = 0;
+        b->pending = ck_pending[(size_t)c];
+        for (int64_t j = 0; j < s1 - s0; ++j) {
+            BCK(cudaMemcpyAsync(inner(j), b->pool[b->side], pb, cudaMemcpyDeviceToDevice, b->stream), "step state");
+            step_pending[(size_t)j] = b->pending;
+            if ((s = run_step(b)) != ESLBM_OK) return s;
+        }
+        for (int64_t j = s1 - s0 - 1; j >= 0; --j) {
+            int64_t pend = step_pending[(size_t)j];
+            const StageList sl = step_stage_list(b, pend);
+            // the step again, one cooperative launch that keeps every stage's output
+            BatchLaunch B;
+            B.pool[0] = inner(j);
+            B.pool[1] = stage(0);
+            B.inst = b->d_inst();
+            B.items = b->d_items();
+            B.n_items = b->n_items;
+            B.side = 0;
+            B.cnt = b->counters();
+            B.sl = sl;
+            B.P = b->P;
+            B.grid = std::max(1, std::min(b->n_items, b->sms * b->blocks_per_sm));
+            B.stream = b->stream;
+            B.rec = stage(0);
+            B.pool_elems = pool_elems;
+            BCK(launch_batch_step(b->family, b->fp64, b->om, B), "recording step launch");
+            // its adjoint stages in reverse, one cooperative launch
+            BatchAdjointLaunch A;
+            A.step_in = inner(j);
+            A.rec = stage(0);
+            A.pool_elems = pool_elems;
+            A.cot[0] = cot[0];
+            A.cot[1] = cot[1];
+            A.side = g;
+            A.inst = b->d_inst();
+            A.items = b->d_items();
+            A.n_items = b->n_items;
+            A.sl = sl;
+            A.P = b->P;
+            A.grid = std::max(1, std::min(b->n_items, b->sms * adj_bps));
+            A.stream = b->stream;
+            BCK(launch_batch_adjoint_step(b->family, b->fp64, b->om, A), "adjoint step launch");
+            if (sl.n & 1) g ^= 1;
+        }
+    }
+    // dJ/du0 = sum_k E_k(u0)^T g_k for f_0 = f^eq(u0)
+    cell0 = 0;
+    for (int32_t i = 0; i < b->count; ++i) {
+        const BatchInstance &I = b->L.inst[(size_t)i];
         const int64_t off = cell0 * b->L.M;
-        s = eslbm_gradient(h, u0 + off, dJ_duT + off, dJ_du0 + off, n, K, ws, ws_bytes);
-        if (s != ESLBM_OK) b->err = std::string("instance gradient: ") + eslbm_last_error(h);
-        eslbm_destroy(h);
-        if (s != ESLBM_OK) return s;
+        BCK(launch_adjoint_init(b->family, b->fp64, u0 + off, inst_at(cot[g], i), dJ_du0 + off, I.nx * I.ny, b->P,
+                                b->stream),
+            "adjoint init");
         cell0 += I.nx * I.ny;
     }
     // the pools now hold other states: start again from u0 on the next step

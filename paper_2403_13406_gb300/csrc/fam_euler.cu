@@ -31,4 +31,11 @@ cudaError_t batch_euler(bool fp64, const BatchLaunch &L) { return batch_family<E
 
 int batch_occ_euler(bool fp64) { return batch_occ_family<Euler2>(fp64, OM_FIXED); }
 
+cudaError_t batch_adjoint_euler(bool fp64, const BatchAdjointLaunch &L)
+{
+    return batch_adjoint_family<Euler2>(fp64, OM_FIXED, L);
+}
+
+int batch_adjoint_occ_euler(bool fp64) { return batch_adjoint_occ_family<Euler2>(fp64, OM_FIXED); }
+
 }  // namespace eslbm

@@ -339,6 +339,29 @@ bool plan_step2d(int64_t nx, int64_t ny, int planes, int elem, int sms, const St
     return pl.smem <= (size_t)kStep2dSmemBudget;
 }
 
+cudaError_t batch_adjoint_sw2(bool, int, const BatchAdjointLaunch &);
+cudaError_t batch_adjoint_scalar(int, bool, int, const BatchAdjointLaunch &);
+cudaError_t batch_adjoint_euler(bool, const BatchAdjointLaunch &);
+int batch_adjoint_occ_sw2(bool, int);
+int batch_adjoint_occ_scalar(int, bool, int);
+int batch_adjoint_occ_euler(bool);
+
+cudaError_t launch_batch_adjoint_step(int family, bool fp64, int om, const BatchAdjointLaunch &L)
+{
+    if (family == FAM_SW2) return batch_adjoint_sw2(fp64, om, L);
+    if (family == FAM_EULER2) return batch_adjoint_euler(fp64, L);
+    if (family == FAM_LINEAR2 || family == FAM_BURGERS2) return batch_adjoint_scalar(family, fp64, om, L);
+    return cudaErrorInvalidValue;
+}
+
+int batch_adjoint_blocks_per_sm(int family, bool fp64, int om)
+{
+    if (family == FAM_SW2) return batch_adjoint_occ_sw2(fp64, om);
+    if (family == FAM_EULER2) return batch_adjoint_occ_euler(fp64);
+    if (family == FAM_LINEAR2 || family == FAM_BURGERS2) return batch_adjoint_occ_scalar(family, fp64, om);
+    return 0;
+}
+
 int totals_blocks() { return kRedBlocks; }
 
 }  // namespace eslbm

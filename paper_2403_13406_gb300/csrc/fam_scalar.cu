@@ -96,4 +96,18 @@ cudaError_t check_scalar(int family, bool fp64, int om, const Params &P, Counter
     return cudaSuccess;
 }
 
+cudaError_t batch_adjoint_scalar(int family, bool fp64, int om, const BatchAdjointLaunch &L)
+{
+    if (family == FAM_LINEAR2) return batch_adjoint_family<Scalar<2, false>>(fp64, om, L);
+    if (family == FAM_BURGERS2) return batch_adjoint_family<Scalar<2, true>>(fp64, om, L);
+    return cudaErrorInvalidValue;
+}
+
+int batch_adjoint_occ_scalar(int family, bool fp64, int om)
+{
+    if (family == FAM_LINEAR2) return batch_adjoint_occ_family<Scalar<2, false>>(fp64, om);
+    if (family == FAM_BURGERS2) return batch_adjoint_occ_family<Scalar<2, true>>(fp64, om);
+    return 0;
+}
+
 }  // namespace eslbm

@@ -48,4 +48,11 @@ cudaError_t check_sw2(bool fp64, int om, const Params &P, Counters *cnt, cudaStr
     return check_family<ShallowWater<2>>(fp64, om, P, cnt, st);
 }
 
+cudaError_t batch_adjoint_sw2(bool fp64, int om, const BatchAdjointLaunch &L)
+{
+    return batch_adjoint_family<ShallowWater<2>>(fp64, om, L);
+}
+
+int batch_adjoint_occ_sw2(bool fp64, int om) { return batch_adjoint_occ_family<ShallowWater<2>>(fp64, om); }
+
 }  // namespace eslbm

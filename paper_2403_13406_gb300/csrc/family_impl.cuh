@@ -177,7 +177,8 @@ cudaError_t adjoint_init_family(bool fp64, const double *u0, const void *g, doub
 template <class Sys, class R, int OM>
 cudaError_t batch_one(const BatchLaunch &L)
 {
-    BatchArgs<R> a{{(R *)L.pool[0], (R *)L.pool[1]}, L.inst, L.items, L.n_items, L.side, L.cnt};
+    BatchArgs<R> a{{(R *)L.pool[0], (R *)L.pool[1]}, L.inst, L.items, L.n_items, L.side, L.cnt, (R *)L.rec,
+                   L.pool_elems};
     StageList sl = L.sl;
     ParamsR<R> P = params_as<R>(L.P);
     void *args[] = {&a, &sl, &P};
@@ -211,6 +212,42 @@ template <class Sys>
 int batch_occ_family(bool fp64, int om)
 {
     return fp64 ? batch_occ_prec<Sys, double>(om) : batch_occ_prec<Sys, float>(om);
+}
+
+template <class Sys, class R>
+cudaError_t batch_adjoint_prec(int om, const BatchAdjointLaunch &L)
+{
+    BatchAdjointArgs<R> a{(const R *)L.step_in, (const R *)L.rec, L.pool_elems, {(R *)L.cot[0], (R *)L.cot[1]},
+                          L.side, L.inst, L.items, L.n_items};
+    StageList sl = L.sl;
+    ParamsR<R> P = params_as<R>(L.P);
+    void *args[] = {&a, &sl, &P};
+    return with_variant<Sys, R>(om, [&]<int OM>() {
+        return cudaLaunchCooperativeKernel((const void *)k_batch_adjoint_step<Sys, R, OM>, dim3((unsigned)L.grid),
+                                           dim3(kBlock), args, 0, L.stream);
+    });
+}
+
+template <class Sys>
+cudaError_t batch_adjoint_family(bool fp64, int om, const BatchAdjointLaunch &L)
+{
+    return fp64 ? batch_adjoint_prec<Sys, double>(om, L) : batch_adjoint_prec<Sys, float>(om, L);
+}
+
+template <class Sys, class R>
+int batch_adjoint_occ_prec(int om)
+{
+    int n = 0;
+    cudaError_t e = with_variant<Sys, R>(om, [&]<int OM>() {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_adjoint_step<Sys, R, OM>, kBlock, 0);
+    });
+    return e == cudaSuccess ? n : 0;
+}
+
+template <class Sys>
+int batch_adjoint_occ_family(bool fp64, int om)
+{
+    return fp64 ? batch_adjoint_occ_prec<Sys, double>(om) : batch_adjoint_occ_prec<Sys, float>(om);
 }
 
 template <class Sys, class R, int OM>

@@ -664,6 +664,10 @@ template <class R> struct BatchArgs {
     int n_items;
     int side;  // pool holding the state on entry
     Counters *cnt;
+    // recording (reverse mode): when set, stage st reads pool[side] (st = 0) or rec + (st - 1) pool_elems
+    // and writes rec + st pool_elems, so every stage's output is kept; the pools are not written
+    R *rec;
+    int64_t pool_elems;
 };
 
 template <class Sys, class R, int OM>
@@ -673,8 +677,8 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchArgs<R> a, StageList
     cg::grid_group grid = cg::this_grid();
     int side = a.side;
     for (int st = 0; st < sl.n; ++st) {
-        const R *__restrict__ fin = a.pool[side];
-        R *__restrict__ fout = a.pool[side ^ 1];
+        const R *__restrict__ fin = (a.rec && st > 0) ? a.rec + (int64_t)(st - 1) * a.pool_elems : a.pool[side];
+        R *__restrict__ fout = a.rec ? a.rec + (int64_t)st * a.pool_elems : a.pool[side ^ 1];
         const int s = sl.shift[st], kind = sl.kind[st];
         for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
             const BatchItem w = a.items[it];
@@ -707,6 +711,70 @@ __global__ void __launch_bounds__(kBlock) k_batch_step(BatchArgs<R> a, StageList
                     for (int i = 0; i < Q * M; ++i) fo[(int64_t)i * ncell + o] = f[i];
                 }
                 if constexpr (checked<Sys, OM>()) warp_count(fb, &a.cnt->fallbacks);
+            }
+        }
+        side ^= 1;
+        grid.sync();
+    }
+}
+
+// Batched reverse mode: the adjoint stages of one composite step of every instance in one
+// cooperative launch, in reverse stage order with a grid barrier between stages.  Stage st's
+// forward input is step_in (st = 0) or the recorded output of stage st - 1; the cotangent
+// ping-pongs between cot[side] (the step output's on entry) and cot[side ^ 1].  Per cell the
+// arithmetic is that of k_adjoint_stage: the transposed relaxation Jacobian, scattered by the
+// reverse shift (each input cell receives exactly one contribution).
+template <class R> struct BatchAdjointArgs {
+    const R *step_in;
+    const R *rec;
+    int64_t pool_elems;
+    R *cot[2];
+    int side;
+    const BatchInstance *inst;
+    const BatchItem *items;
+    int n_items;
+};
+
+template <class Sys, class R, int OM>
+__global__ void __launch_bounds__(kBlock) k_batch_adjoint_step(BatchAdjointArgs<R> a, StageList sl, ParamsR<R> P)
+{
+    constexpr int Q = Sys::Q, M = Sys::M;
+    cg::grid_group grid = cg::this_grid();
+    int side = a.side;
+    for (int st = sl.n - 1; st >= 0; --st) {
+        const R *__restrict__ fin = st > 0 ? a.rec + (int64_t)(st - 1) * a.pool_elems : a.step_in;
+        const R *__restrict__ gout = a.cot[side];
+        R *__restrict__ gin = a.cot[side ^ 1];
+        const int s = sl.shift[st], kind = sl.kind[st];
+        for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+            const BatchItem w = a.items[it];
+            const BatchInstance I = a.inst[w.inst];
+            const int64_t ncell = I.nx * I.ny;
+            Shift sh;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const int64_t n = Lattice<2>::axis(k) == 0 ? I.nx : I.ny;
+                int64_t r = (-(int64_t)Lattice<2>::sign(k) * s) % n;
+                sh.roff[k] = r < 0 ? r + n : r;
+            }
+            for (int j = threadIdx.x; j < w.nx; j += blockDim.x) {
+                const int64_t x = w.x0 + j, y = w.y, o = y * I.nx + x;
+                int64_t src[Q];
+                R f[Q * M], go[Q * M], gi[Q * M];
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    src[k] = src_cell<2>(k, x, y, I.nx, I.ny, sh);
+#pragma unroll
+                    for (int m = 0; m < M; ++m) {
+                        f[k * M + m] = fin[I.offset + (int64_t)(k * M + m) * ncell + src[k]];
+                        go[k * M + m] = gout[I.offset + (int64_t)(k * M + m) * ncell + o];
+                    }
+                }
+                relax_adjoint<Sys, R, OM>(P, f, go, kind, gi);
+#pragma unroll
+                for (int k = 0; k < Q; ++k)
+#pragma unroll
+                    for (int m = 0; m < M; ++m) gin[I.offset + (int64_t)(k * M + m) * ncell + src[k]] = gi[k * M + m];
             }
         }
         side ^= 1;

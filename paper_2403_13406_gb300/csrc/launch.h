@@ -114,10 +114,31 @@ struct BatchLaunch {
     Params P;
     int grid;  // blocks (all resident: cooperative launch)
     cudaStream_t stream;
+    void *rec = nullptr;     // reverse mode: keep every stage's output at rec + st * pool_elems
+    int64_t pool_elems = 0;  // elements of one pool
 };
 
 // one composite step of every instance of a 2D batch (cooperative, grid.sync between stages)
 cudaError_t launch_batch_step(int family, bool fp64, int om, const BatchLaunch &L);
+
+struct BatchAdjointLaunch {
+    const void *step_in;  // forward input of the step (a pool)
+    const void *rec;      // outputs of its stages 0 .. n-2 (pools)
+    int64_t pool_elems;
+    void *cot[2];         // cotangent pools; cot[side] holds the step output's cotangent on entry
+    int side;
+    const BatchInstance *inst;
+    const BatchItem *items;
+    int n_items;
+    StageList sl;
+    Params P;
+    int grid;
+    cudaStream_t stream;
+};
+
+// the adjoint stages of one step of every instance (cooperative, reverse order)
+cudaError_t launch_batch_adjoint_step(int family, bool fp64, int om, const BatchAdjointLaunch &L);
+int batch_adjoint_blocks_per_sm(int family, bool fp64, int om);
 // resident blocks per SM of that kernel (0 if the family has no batched kernel)
 int batch_blocks_per_sm(int family, bool fp64, int om);
 

@@ -25,7 +25,7 @@ CASES = {
     # 1D: one temporally blocked launch per composite step
     "sw1d": (1, "sw", 1000, 1, dict(V=4.0, g=9.81), lambda: inputs.sw_random_1d(1000, seed=3, h_amp=0.2, u_amp=0.3)),
     "burgers1d": (1, "burgers", 1000, 1, dict(V=1.5), lambda: inputs.random_scalar_1d(1000, seed=2)),
-    # 2D rows on 16-byte boundaries: the bulk-copy staged stage kernel
+    # 2D rows on 16-byte boundaries: the bulk-copy staged stage kernel, or the blocked 2D kernel
     "sw2d_rows": (2, "sw", 1032, 3, dict(V=8.0, g=9.81),
                   lambda: inputs.sw_random_2d(1032, 3, seed=9, h_amp=0.1, u_amp=0.2)),
     "burgers2d_rows": (2, "burgers", 1032, 6, dict(V=3.0, c=(1.0, 0.6)),
@@ -48,10 +48,10 @@ def run(name, precision, diag, steps=6, blocking=True):
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("precision", ["fp32", "fp64", "fp32_mixed"])
-@pytest.mark.parametrize("blocking", [True, False])
+@pytest.mark.parametrize("blocking", [True, False, 6])
 def test_diagnostics_leave_results_unchanged(name, precision, blocking):
-    """blocking on: the 1D and 2D temporally blocked kernels; off: the per-stage kernels (2D rows on
-    16-byte boundaries: the bulk-copy staged stage kernel)."""
+    """Default: the 1D temporally blocked kernel, the 2D per-stage kernel (rows on 16-byte boundaries:
+    the bulk-copy staged one); off: the per-stage kernels; 6: the temporally blocked 2D kernel."""
     f0, d0 = run(name, precision, False, blocking=blocking)
     f1, d1 = run(name, precision, True, blocking=blocking)
     assert np.array_equal(f0, f1)
