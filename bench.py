@@ -180,7 +180,7 @@ def oracle_rate(workload, openmp):
         desc = "Euler isentropic vortex %d^2, %d composite steps (scheme I, omega = 2)" % (n, steps)
         cells = n * n
     else:
-        n, steps = (1 << 15, 2) if (openmp and used) else (1 << 12, 2)
+        n, steps = (1 << 14, 2) if (openmp and used) else (1 << 11, 2)
         m = O.Model(1, "sw", n, V=SW_V, g=G, omega_mode="entropic")
         f = O.init_equilibrium(m, inputs.sw_sine_1d(n, 1.0, 0.1))
         desc = "1D shallow water N = %d, %d composite steps (entropic omega)" % (n, steps)
@@ -606,14 +606,16 @@ def adjoint_leg(torch, eslbm, inputs, stream, dev, N=1 << 16, n=96, K=16):
                                    "adjoint_s": times["adjoint"], "ratio": times["adjoint"] / times["forward"]}}
 
 
-def batch_leg(torch, eslbm, inputs, stream, dev, count=64, steps=BATCH_STEPS, K=BATCH_K, grad=True):
+def batch_leg(torch, eslbm, inputs, stream, dev, count=64, steps=BATCH_STEPS, K=BATCH_K, grad=True, grad_steps=None):
     """Batched form: `count` 2D shallow-water instances (D2Q4, FP32 shifted by the state at rest of depth
     1, entropic) of uneven seeded sizes in [256, 1024]^2 with 8-mode Fourier depth data, advanced by one
     cooperative launch per composite step replayed from CUDA graphs, after the autotuner has picked the
     schedule, for `steps` composite steps; then the reverse mode: the gradient of the L2 misfit of the
     final depth against a seeded target with respect to the initial depth of every instance,
-    checkpoints every K steps.  The FP32 error after the steps is stated against FP64 single-lattice
-    runs of two instances."""
+    checkpoints every K steps (grad_steps composite steps: the full run by default, fewer in the
+    default bench line to bound its time).  The FP32 error after the steps is stated against FP64
+    single-lattice runs of two instances."""
+    grad_steps = steps if grad_steps is None else grad_steps
     sizes = inputs.batched_sizes(count, 256, 1024)
     cfg = eslbm.make_config(2, "sw", 1, 1, V=BATCH_V, g=G, precision="fp32", omega_mode="entropic",
                             u_ref=(1.0, 0.0, 0.0))
@@ -662,7 +664,7 @@ def batch_leg(torch, eslbm, inputs, stream, dev, count=64, steps=BATCH_STEPS, K=
             torch.cuda.synchronize(dev)
             tf = time.perf_counter()
             b.init_equilibrium(u0)
-            b.step(steps)
+            b.step(grad_steps)
             uT = b.moments_flat()
             torch.cuda.synchronize(dev)
             fwd_s = time.perf_counter() - tf
@@ -671,10 +673,10 @@ def batch_leg(torch, eslbm, inputs, stream, dev, count=64, steps=BATCH_STEPS, K=
                 b.unpack(lam)[v][0] = 2.0 * (u[0] - t[0])  # dJ/dh_T of J = sum (h_T - target)^2
             torch.cuda.synchronize(dev)
             ta = time.perf_counter()
-            g = b.gradient(u0, lam, steps, K)
+            g = b.gradient(u0, lam, grad_steps, K)
             torch.cuda.synchronize(dev)
             adj_s = time.perf_counter() - ta
-            out["adjoint"] = {"instances": count, "steps": steps, "checkpoint_every": K, "forward_s": fwd_s,
+            out["adjoint"] = {"instances": count, "steps": grad_steps, "checkpoint_every": K, "forward_s": fwd_s,
                               "gradient_s": adj_s, "ratio": adj_s / fwd_s, "grad_norm": float(torch.linalg.vector_norm(g)),
                               "finite": bool(torch.isfinite(g).all())}
         b.close()
@@ -717,6 +719,8 @@ def main():
         dev = torch.device("cuda", 0)
         stream = torch.cuda.Stream(device=dev)
         kw = {"count": args.batch_count} if args.leg == "batched" else {}
+        if args.leg == "precision" and args.n != EULER_N:
+            kw = {"N": args.n}  # e.g. --leg precision --n 1048576: the 1D grid of the 1D workload
         print(json.dumps(LEGS[args.leg](torch, eslbm, inputs, stream, dev, **kw)), flush=True)
         return
 
@@ -739,7 +743,8 @@ def main():
         for leg in (sw1d_leg, burgers2d_leg, riemann_leg, blocked2d_leg, precision_leg, fp32_vs_fp64_leg,
                     accuracy_leg, adjoint_leg):
             extras.update(leg(torch, eslbm, inputs, stream, dev))
-        extras.update(batch_leg(torch, eslbm, inputs, stream, dev, count=args.batch_count))
+        extras.update(batch_leg(torch, eslbm, inputs, stream, dev, count=args.batch_count, grad_steps=100,
+                                K=10))
     if rank == 0 and world == 1 and not args.no_extras:
         c = cpu_leg()["cpu_oracle"]
         extras["cpu_oracle"] = c
