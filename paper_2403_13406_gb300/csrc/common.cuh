@@ -136,7 +136,7 @@ struct StageList {
 #endif
 constexpr int kStep2dThreads = ESLBM_STEP2D_THREADS;             // threads of a block (most variants)
 constexpr int kStep2dSlots = 8;                                   // items (stage, column) a thread owns
-constexpr int kStep2dMaxItems = kStep2dSlots * 256;               // items of a tick (smallest block: 256)
+constexpr int kStep2dMaxItems = kStep2dSlots * (256 - 32);        // items of a tick (smallest block: 256)
 constexpr int kStep2dBlocksPerSm = ESLBM_STEP2D_BLOCKS_PER_SM;  // resident blocks per SM (shared memory split)
 constexpr int kStep2dPrefetch = ESLBM_STEP2D_PREFETCH;          // window rows loaded ahead of use
 constexpr int kStep2dMaxStages = 32;

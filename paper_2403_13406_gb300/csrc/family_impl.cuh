@@ -256,12 +256,12 @@ cudaError_t step2d_one(const Step2dLaunch &L)
     if (!stage_list_ok(L.sl) || L.sl.n > kStep2dMaxStages) return cudaErrorInvalidValue;
     const Plan2d &pl = L.plan;
     if (pl.ring > kStep2dMaxRing || pl.smem > (size_t)kStep2dSmemBudget) return cudaErrorInvalidValue;
-    // threads: the items of a tick spread evenly over at most the variant's threads, at most
-    // kStep2dSlots items a thread
-    constexpr int tmax = Step2dThreads<Sys, R, OM>::value;
-    const int nslots = (pl.items + tmax - 1) / tmax;
+    // threads: a producer warp, and consumers over which the items of a tick spread evenly (at most
+    // the variant's threads in all, at most kStep2dSlots items a consumer)
+    constexpr int cmax = Step2dThreads<Sys, R, OM>::value - 32;
+    const int nslots = (pl.items + cmax - 1) / cmax;
     if (nslots < 1 || nslots > kStep2dSlots) return cudaErrorInvalidValue;
-    const int threads = ((pl.items + nslots - 1) / nslots + 31) / 32 * 32;
+    const int threads = 32 + ((pl.items + nslots - 1) / nslots + 31) / 32 * 32;
     static std::atomic<int> attr[kMaxDevices];
     const int d = device_slot();
     if (!attr[d].load()) {

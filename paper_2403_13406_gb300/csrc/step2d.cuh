@@ -17,8 +17,9 @@
 // so a stage relaxes each cell in place (it reads and writes the same four
 // slots).  Stage j handles one row per tick, lagging stage j - 1 by |s_j| + 1
 // rows (stage 1 lags the load by |s_1|): every value it reads was written in an
-// earlier tick, and one barrier per tick orders the stages.  A thread owns the
-// same (stage, column) items every tick.  Stage j computes
+// earlier tick, and one barrier per tick (among the consumer warps) orders the
+// stages.  A consumer thread owns the same (stage, column) items every tick; a
+// producer warp issues the rows' copies.  Stage j computes
 // only the cells that can still reach the output (rows and columns within
 // H - m_j of it, m_j = |s_1| + ... + |s_j|), which are exactly the cells whose
 // inputs stage j - 1 computed.  The last stage writes the output rows straight
@@ -73,6 +74,7 @@ __global__ void __launch_bounds__(Step2dThreads<Sys, R, OM>::value, kStep2dBlock
     R *ring = reinterpret_cast<R *>(smem2d + kStep2dBarBytes);
     __shared__ int sLag[kStep2dMaxStages], sM[kStep2dMaxStages], sAcc[kStep2dMaxStages], sKind[kStep2dMaxStages];
     __shared__ int sOff[kStep2dMaxStages + 1];
+    __shared__ int sTickDone, sFail, sIssued;  // ticks the consumers finished, failure flag, rows issued
     const int G = sl.n, H = sl.halo;
     const int64_t x0 = (int64_t)(blockIdx.x % a.nstrips) * a.tx;
     const int64_t y0 = (int64_t)(blockIdx.x / a.nstrips) * a.ly;
@@ -96,6 +98,9 @@ __global__ void __launch_bounds__(Step2dThreads<Sys, R, OM>::value, kStep2dBlock
             off += tx + 2 * (H - m);
         }
         sOff[G] = off;
+        sTickDone = 0;
+        sFail = 0;
+        sIssued = 0;
         for (int i = 0; i < a.ring; ++i)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -141,116 +146,140 @@ __global__ void __launch_bounds__(Step2dThreads<Sys, R, OM>::value, kStep2dBlock
             }
         }
     };
-    if (threadIdx.x < 32)
-        for (int r = 0; r < a.prefetch && r < nrows; ++r) load_row(r);
-
-    // The items of a tick (stage j, window column c) are the same every tick: each thread owns items
-    // threadIdx.x + s * blockDim.x, s < kStep2dSlots, and keeps their stage and column in registers.
-    int slot_j[kStep2dSlots], slot_c[kStep2dSlots];
-#pragma unroll
-    for (int s = 0; s < kStep2dSlots; ++s) {
-        const int idx = s * (int)blockDim.x + (int)threadIdx.x;
-        int j = -1, c = 0;
-        if (idx < items) {
-            j = 0;
-            while (idx >= sOff[j + 1]) ++j;
-            c = a.hl - H + sM[j] + (idx - sOff[j]);
-        }
-        slot_j[s] = j;
-        slot_c[s] = c;
-    }
-    const int nslots = (items + (int)blockDim.x - 1) / (int)blockDim.x;  // <= kStep2dSlots (planner)
-
+    // Warp 0 is the producer: it issues the rows' bulk copies, row r once the consumers have finished
+    // tick r - prefetch (the last tick that reads the slot it overwrites; ring >= prefetch + the
+    // longest lifetime of a row), which they publish in sTickDone (release / acquire).  The other
+    // warps are the consumers: they wait for each row's copies on its mbarrier, relax, and meet at a
+    // named barrier that only they use, once per tick.  All waits are bounded; a consumer that gives
+    // up sets sFail before the tick's barrier, so that all consumers leave together.
+    const int nconsumers = (int)blockDim.x - 32;
     int failed_tick = -1;
-    for (int tau = 0; tau < ticks; ++tau) {
-        // row tau of the window has arrived (bounded wait; the block agrees at the tick's barrier)
-        uint32_t done = 1;
-        if (tau < nrows) {
-            const uint32_t bar = smem_u32(&bars[ring_row(tau)]);
-            const uint32_t parity = (uint32_t)((tau / a.ring) & 1);
-            done = 0;
-            for (int it = 0; it < (1 << 22) && !done; ++it) {
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\t"
-                    "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                    "selp.u32 %0, 1, 0, p;\n\t}"
-                    : "=r"(done)
-                    : "r"(bar), "r"(parity)
-                    : "memory");
+    if (threadIdx.x < 32) {
+        for (int r = 0; r < nrows; ++r) {
+            if (r >= a.prefetch) {
+                int ok = 0;
+                if (threadIdx.x == 0) {  // lane 0 waits; the decision is the warp's
+                    for (int it = 0; it < (1 << 24) && !ok; ++it) {
+                        int d, f;
+                        asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];"
+                                     : "=r"(d)
+                                     : "r"(smem_u32(&sTickDone))
+                                     : "memory");
+                        asm volatile("ld.relaxed.cta.shared::cta.b32 %0, [%1];" : "=r"(f) : "r"(smem_u32(&sFail)) : "memory");
+                        if (f) break;
+                        ok = d >= r - a.prefetch + 1;
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) break;  // the consumers gave up (or never got there): issue nothing more
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             }
+            load_row(r);
+            if (threadIdx.x == 0) sIssued = r + 1;
         }
+    } else {
+        // The items of a tick (stage j, window column c) are the same every tick: consumer ct owns
+        // items ct + s * nconsumers, s < kStep2dSlots, and keeps their stage and column in registers.
+        const int ct = (int)threadIdx.x - 32;
+        int slot_j[kStep2dSlots], slot_c[kStep2dSlots];
 #pragma unroll
         for (int s = 0; s < kStep2dSlots; ++s) {
-            if (s >= nslots) break;  // uniform: every warp runs the same slots (warp-level counters)
-            const int j = slot_j[s];
-            const int r = j >= 0 ? tau - sLag[j] : -1;
-            const bool valid = done && j >= 0 && r >= sM[j] && r < nrows - sM[j];
-            bool fb = false, counted = false;
-            if (valid) {
-                const int c = slot_c[s];
-                const int acc = sAcc[j];
-                // element offsets of the four populations' slots (plane 0 of each): rows r, r - acc,
-                // r + acc of the ring (r >= m_j >= |acc_j|), columns c -+ acc
-                const int b0 = ring_row(r) * rowstride;
-                int off[Q];
-                off[0] = b0 + c - acc;                           // +x
-                off[1] = ring_row(r - acc) * rowstride + c;      // +y
-                off[2] = b0 + c + acc;                           // -x
-                off[3] = ring_row(r + acc) * rowstride + c;      // -y
-                R f[NP];
-#pragma unroll
-                for (int k = 0; k < Q; ++k)
-#pragma unroll
-                    for (int m = 0; m < M; ++m) f[k * M + m] = ring[off[k] + (k * M + m) * a.wx];
-                // output cells count and record (each cell-stage once over all blocks)
-                counted = r >= H && r < H + ly && c >= a.hl && c < a.hl + tx;
-                const int64_t cell = (y0 + r - H) * a.nx + (x0 + c - a.hl);
-                relax_cell<Sys, R, OM>(P, f, sKind[j], fb, record_of<Sys, R, OM>(P, j, cell, counted));
-                if (j == G - 1) {
-#pragma unroll
-                    for (int p = 0; p < NP; ++p) a.fout[(int64_t)p * a.ncell + cell] = f[p];
-                } else {
-#pragma unroll
-                    for (int k = 0; k < Q; ++k)
-#pragma unroll
-                        for (int m = 0; m < M; ++m) ring[off[k] + (k * M + m) * a.wx] = f[k * M + m];
-                }
+            const int idx = s * nconsumers + ct;
+            int j = -1, c = 0;
+            if (idx < items) {
+                j = 0;
+                while (idx >= sOff[j + 1]) ++j;
+                c = a.hl - H + sM[j] + (idx - sOff[j]);
             }
-            if constexpr (checked<Sys, OM>()) warp_count(fb && counted, &a.cnt->fallbacks);
+            slot_j[s] = j;
+            slot_c[s] = c;
         }
-        // every read of this tick is done: the slot of row tau + prefetch (last read in this tick or
-        // before) is reloaded, while the other warps go on with the next tick
-        if (__syncthreads_or(!done)) {
-            failed_tick = tau;
-            break;
-        }
-        if (threadIdx.x < 32 && tau + a.prefetch < nrows) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            load_row(tau + a.prefetch);
-        }
-    }
-    if (failed_tick >= 0) {
-        // a copy never arrived (not expected): report it, and before leaving wait (bounded) for
-        // the copies still in flight into this block's shared memory
-        if (threadIdx.x == 0) {
-            atomicAdd(&a.cnt->copy_timeouts, 1ull);
-            const int issued = min(nrows, failed_tick + a.prefetch);
-            for (int r = failed_tick; r < issued; ++r) {
-                const uint32_t bar = smem_u32(&bars[ring_row(r)]);
-                const uint32_t parity = (uint32_t)((r / a.ring) & 1);
-                uint32_t ok = 0;
-                for (int it = 0; it < (1 << 22) && !ok; ++it) {
+        const int nslots = (items + nconsumers - 1) / nconsumers;  // <= kStep2dSlots (launcher)
+        for (int tau = 0; tau < ticks; ++tau) {
+            // row tau of the window has arrived (bounded wait)
+            uint32_t done = 1;
+            if (tau < nrows) {
+                const uint32_t bar = smem_u32(&bars[ring_row(tau)]);
+                const uint32_t parity = (uint32_t)((tau / a.ring) & 1);
+                done = 0;
+                for (int it = 0; it < (1 << 22) && !done; ++it) {
                     asm volatile(
                         "{\n\t.reg .pred p;\n\t"
                         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                         "selp.u32 %0, 1, 0, p;\n\t}"
-                        : "=r"(ok)
+                        : "=r"(done)
                         : "r"(bar), "r"(parity)
                         : "memory");
                 }
+                if (!done) atomicOr(&sFail, 1);
+            }
+#pragma unroll
+            for (int s = 0; s < kStep2dSlots; ++s) {
+                if (s >= nslots) break;  // uniform: every warp runs the same slots (warp-level counters)
+                const int j = slot_j[s];
+                const int r = j >= 0 ? tau - sLag[j] : -1;
+                const bool valid = done && j >= 0 && r >= sM[j] && r < nrows - sM[j];
+                bool fb = false, counted = false;
+                if (valid) {
+                    const int c = slot_c[s];
+                    const int acc = sAcc[j];
+                    // element offsets of the four populations' slots (plane 0 of each): rows r, r - acc,
+                    // r + acc of the ring (r >= m_j >= |acc_j|), columns c -+ acc
+                    const int b0 = ring_row(r) * rowstride;
+                    int off[Q];
+                    off[0] = b0 + c - acc;                       // +x
+                    off[1] = ring_row(r - acc) * rowstride + c;  // +y
+                    off[2] = b0 + c + acc;                       // -x
+                    off[3] = ring_row(r + acc) * rowstride + c;  // -y
+                    R f[NP];
+#pragma unroll
+                    for (int k = 0; k < Q; ++k)
+#pragma unroll
+                        for (int m = 0; m < M; ++m) f[k * M + m] = ring[off[k] + (k * M + m) * a.wx];
+                    // output cells count and record (each cell-stage once over all blocks)
+                    counted = r >= H && r < H + ly && c >= a.hl && c < a.hl + tx;
+                    const int64_t cell = (y0 + r - H) * a.nx + (x0 + c - a.hl);
+                    relax_cell<Sys, R, OM>(P, f, sKind[j], fb, record_of<Sys, R, OM>(P, j, cell, counted));
+                    if (j == G - 1) {
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) a.fout[(int64_t)p * a.ncell + cell] = f[p];
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < Q; ++k)
+#pragma unroll
+                            for (int m = 0; m < M; ++m) ring[off[k] + (k * M + m) * a.wx] = f[k * M + m];
+                    }
+                }
+                if constexpr (checked<Sys, OM>()) warp_count(fb && counted, &a.cnt->fallbacks);
+            }
+            // every read and write of this tick is done
+            asm volatile("bar.sync 1, %0;" ::"r"(nconsumers) : "memory");
+            if (*(volatile int *)&sFail) {
+                failed_tick = tau;
+                break;
+            }
+            if (ct == 0) asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sTickDone)), "r"(tau + 1) : "memory");
+        }
+    }
+    __syncthreads();  // producer and consumers: every copy that will be issued has been issued
+    if (failed_tick >= 0 && threadIdx.x == 32) {
+        // a copy never arrived (not expected): report it, and before leaving wait (bounded) for the
+        // copies still in flight into this block's shared memory
+        atomicAdd(&a.cnt->copy_timeouts, 1ull);
+        for (int r = failed_tick; r < sIssued; ++r) {
+            const uint32_t bar = smem_u32(&bars[ring_row(r)]);
+            const uint32_t parity = (uint32_t)((r / a.ring) & 1);
+            uint32_t ok = 0;
+            for (int it = 0; it < (1 << 22) && !ok; ++it) {
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                    "selp.u32 %0, 1, 0, p;\n\t}"
+                    : "=r"(ok)
+                    : "r"(bar), "r"(parity)
+                    : "memory");
             }
         }
-        __syncthreads();
     }
 }
 

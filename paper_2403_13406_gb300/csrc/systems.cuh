@@ -25,6 +25,22 @@ namespace eslbm {
 template <class R> __device__ __forceinline__ R qdiv(R a, R b) { return a / b; }
 template <> __device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
 
+// The equilibria base + d and base - d of two opposite populations, with a sum of exactly 2 base:
+// the one away from zero is rounded, the other is 2 base minus it, which is exact by Sterbenz's
+// lemma when |d| <= 3 |base| (always for the mass component in the convexity domain; a single
+// rounding otherwise).  Rounded independently, the pair lands in different binades whenever
+// |d| is a sizeable fraction of |base|, and the two roundings then leave a bias in the sum that
+// the relaxation turns into a steady drift of the conserved moments (FP32: 3e-9 of the mass per
+// cell-stage on 2D Burgers).
+template <class R> __host__ __device__ __forceinline__ void eq_pair(R base, R d, R &plus, R &minus)
+{
+    const bool same = (base >= R(0)) == (d >= R(0));
+    const R big = same ? base + d : base - d;
+    const R other = (base + base) - big;
+    plus = same ? big : other;
+    minus = same ? other : big;
+}
+
 // ---------------------------------------------------------------------------
 // Scalar systems (M = 1): linear transport and Burgers.  Dual kinetic
 // entropies s*_k(p) = p^2/(2Q) + sign_k G^{j*}(p)/(2V) (Examples 1, 2, 4 and
@@ -52,11 +68,9 @@ template <int DIM, bool BURGERS> struct Scalar {
         const R phi0 = flux<R>(P, 0, u[0]);
         const R phi1 = DIM == 2 ? flux<R>(P, 1, u[0]) : R(0);
         const R base = u[0] / R(Q);
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            const R phi = Lattice<DIM>::axis(k) == 0 ? phi0 : phi1;
-            feq[k] = Lattice<DIM>::sign(k) > 0 ? base + phi * inv2V : base - phi * inv2V;
-        }
+        // populations k and k + Q/2 are opposite (+x/-x, +y/-y)
+        eq_pair<R>(base, phi0 * inv2V, feq[0], feq[Q / 2]);
+        if (DIM == 2) eq_pair<R>(base, phi1 * inv2V, feq[1], feq[3]);
     }
 
     // f^eq_k(ubar + du) - f^eq_k(ubar) (u = ubar + du) without cancellation:
@@ -68,11 +82,8 @@ template <int DIM, bool BURGERS> struct Scalar {
 #pragma unroll
         for (int j = 0; j < DIM; ++j) dphi[j] = BURGERS ? P.c[j] * R(0.5) * du[0] * (u[0] + P.ubar[0]) : P.a[j] * du[0];
         const R base = du[0] / R(Q);
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            const R dp = dphi[Lattice<DIM>::axis(k)];
-            fd[k] = Lattice<DIM>::sign(k) > 0 ? base + dp * inv2V : base - dp * inv2V;
-        }
+        eq_pair<R>(base, dphi[0] * inv2V, fd[0], fd[Q / 2]);
+        if (DIM == 2) eq_pair<R>(base, dphi[1] * inv2V, fd[1], fd[3]);
     }
 
     // convexity of every s*_k at the equilibrium dual p = u
@@ -181,15 +192,13 @@ template <int DIM> struct ShallowWater {
             phi[1][1] = u[1] * vy;
             phi[1][2] = u[2] * vy + hp;
         }
+        // populations k and k + Q/2 are opposite (+x/-x, +y/-y)
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
+        for (int k = 0; k < Q / 2; ++k) {
             const int j = Lattice<DIM>::axis(k);
-            const bool plus = Lattice<DIM>::sign(k) > 0;
 #pragma unroll
-            for (int m = 0; m < M; ++m) {
-                const R base = u[m] / R(Q);
-                feq[k * M + m] = plus ? base + phi[j][m] * inv2V : base - phi[j][m] * inv2V;
-            }
+            for (int m = 0; m < M; ++m)
+                eq_pair<R>(u[m] / R(Q), phi[j][m] * inv2V, feq[k * M + m], feq[(k + Q / 2) * M + m]);
         }
     }
 
@@ -219,14 +228,11 @@ template <int DIM> struct ShallowWater {
         }
         const R inv2V = P.inv2V;
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
+        for (int k = 0; k < Q / 2; ++k) {
             const int j = Lattice<DIM>::axis(k);
-            const bool plus = Lattice<DIM>::sign(k) > 0;
 #pragma unroll
-            for (int m = 0; m < M; ++m) {
-                const R base = du[m] / R(Q);
-                fd[k * M + m] = plus ? base + dphi[j][m] * inv2V : base - dphi[j][m] * inv2V;
-            }
+            for (int m = 0; m < M; ++m)
+                eq_pair<R>(du[m] / R(Q), dphi[j][m] * inv2V, fd[k * M + m], fd[(k + Q / 2) * M + m]);
         }
     }
 
@@ -456,15 +462,11 @@ struct Euler2 {
         const R phx[4] = {mx, mx * vx + p, my * vx, vx * (E + p)};
         const R phy[4] = {my, mx * vy, my * vy + p, vy * (E + p)};
         const R inv2V = P.inv2V;
+        // populations k and k + 2 are opposite (+x/-x, +y/-y)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const R *phi = (k & 1) ? phy : phx;
-            const bool plus = k < 2;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const R base = u[m] * R(0.25);
-                feq[k * 4 + m] = plus ? base + phi[m] * inv2V : base - phi[m] * inv2V;
-            }
+        for (int m = 0; m < 4; ++m) {
+            eq_pair<R>(u[m] * R(0.25), phx[m] * inv2V, feq[0 * 4 + m], feq[2 * 4 + m]);
+            eq_pair<R>(u[m] * R(0.25), phy[m] * inv2V, feq[1 * 4 + m], feq[3 * 4 + m]);
         }
     }
 
@@ -490,14 +492,9 @@ struct Euler2 {
                            dvy * Ep + vby * (du[3] + dp)};
         const R inv2V = P.inv2V;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const R *dphi = (k & 1) ? dphy : dphx;
-            const bool plus = k < 2;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const R base = du[m] * R(0.25);
-                fd[k * 4 + m] = plus ? base + dphi[m] * inv2V : base - dphi[m] * inv2V;
-            }
+        for (int m = 0; m < 4; ++m) {
+            eq_pair<R>(du[m] * R(0.25), dphx[m] * inv2V, fd[0 * 4 + m], fd[2 * 4 + m]);
+            eq_pair<R>(du[m] * R(0.25), dphy[m] * inv2V, fd[1 * 4 + m], fd[3 * 4 + m]);
         }
     }
 
