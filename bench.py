@@ -65,9 +65,12 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="headline only (no other workloads, no CPU baseline)")
     p.add_argument("--leg", default=None,
                    choices=["sw1d", "burgers2d", "riemann", "batched", "precision", "accuracy", "adjoint", "cpu",
-                            "blocked2d"],
+                            "blocked2d", "profile"],
                    help="run one secondary measurement alone and print its JSON")
     p.add_argument("--batch-count", type=int, default=64, help="instances of the batched leg")
+    p.add_argument("--case", default="euler",
+                   choices=["euler", "euler_blocked", "sw1d", "burgers2d", "burgers2d_blocked", "batched"],
+                   help="--leg profile: the workload of one short run (for ncu captures)")
     return p.parse_args()
 
 
@@ -699,8 +702,49 @@ def cpu_leg():
 # main
 # ---------------------------------------------------------------------------
 
+def profile_leg(torch, eslbm, inputs, stream, dev, case="euler", n=None, steps=2):
+    """One short run of a workload's kernels, for ncu captures (init, `steps` composite steps,
+    moments): euler = the headline at n x n (default 2048, one launch per stage), euler_blocked =
+    the same through the temporally blocked 2D kernel (6 stages per launch), sw1d = the 1D workload
+    at 2^20 cells, burgers2d[_blocked] = 2D Burgers entropic at n x n (default 4096), batched = 8 of
+    the batched instances."""
+    if case == "batched":
+        sizes = inputs.batched_sizes(8, 256, 1024)
+        cfg = eslbm.make_config(2, "sw", 1, 1, V=BATCH_V, g=G, precision="fp32", omega_mode="entropic",
+                                u_ref=(1.0, 0.0, 0.0))
+        b = eslbm.Batch(cfg, sizes, stream=stream, device=dev)
+        with torch.cuda.stream(stream):
+            b.init_equilibrium(b.pack([inputs.sw_fourier_2d(nx, ny, seed=1000 + i) for i, (nx, ny) in enumerate(sizes)]))
+            b.step(steps)
+            torch.cuda.synchronize(dev)
+        b.close()
+        return {"profile": case, "instances": len(sizes), "steps": steps}
+    if case == "sw1d":
+        N = SW_N
+        cfg = eslbm.make_config(1, "sw", N, V=SW_V, g=G, precision="fp32", omega_mode="entropic", u_ref=SW_UREF)
+        u0 = inputs.sw_sine_1d(N, 1.0, 0.1)
+    elif case.startswith("euler"):
+        N = n or 2048
+        cfg = eslbm.make_config(2, "euler", N, N, V=EULER_V, gamma=EULER_GAMMA, precision="fp32", omega_mode="fixed",
+                                blocking=6 if case.endswith("blocked") else True)
+        u0 = inputs.euler_vortex_2d(N, N)
+    else:
+        N = n or BURGERS_N
+        cfg = eslbm.make_config(2, "burgers", N, N, V=BURGERS_V, precision="fp32", omega_mode="entropic",
+                                blocking=6 if case.endswith("blocked") else True)
+        u0 = inputs.burgers_2d(N, N)
+    with torch.cuda.stream(stream):
+        sim = eslbm.Simulation(cfg, stream=stream, device=dev)
+        sim.init_equilibrium(torch.from_numpy(u0).to(dev))
+        sim.step(steps)
+        sim.moments()
+        torch.cuda.synchronize(dev)
+        sim.close()
+    return {"profile": case, "n": N, "steps": steps}
+
+
 LEGS = {"sw1d": sw1d_leg, "burgers2d": burgers2d_leg, "riemann": riemann_leg, "batched": batch_leg,
-        "blocked2d": blocked2d_leg,
+        "blocked2d": blocked2d_leg, "profile": profile_leg,
         "precision": precision_leg, "accuracy": accuracy_leg, "adjoint": adjoint_leg}
 
 
@@ -721,6 +765,8 @@ def main():
         kw = {"count": args.batch_count} if args.leg == "batched" else {}
         if args.leg == "precision" and args.n != EULER_N:
             kw = {"N": args.n}  # e.g. --leg precision --n 1048576: the 1D grid of the 1D workload
+        if args.leg == "profile":
+            kw = {"case": args.case, "n": None if args.n == EULER_N else args.n}
         print(json.dumps(LEGS[args.leg](torch, eslbm, inputs, stream, dev, **kw)), flush=True)
         return
 
