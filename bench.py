@@ -68,6 +68,7 @@ def parse():
                             "blocked2d", "profile"],
                    help="run one secondary measurement alone and print its JSON")
     p.add_argument("--batch-count", type=int, default=64, help="instances of the batched leg")
+    p.add_argument("--group", type=int, default=6, help="profile leg: stages per blocked 2D launch")
     p.add_argument("--case", default="euler",
                    choices=["euler", "euler_blocked", "sw1d", "burgers2d", "burgers2d_blocked", "batched"],
                    help="--leg profile: the workload of one short run (for ncu captures)")
@@ -702,10 +703,10 @@ def cpu_leg():
 # main
 # ---------------------------------------------------------------------------
 
-def profile_leg(torch, eslbm, inputs, stream, dev, case="euler", n=None, steps=2):
+def profile_leg(torch, eslbm, inputs, stream, dev, case="euler", n=None, steps=2, group=6):
     """One short run of a workload's kernels, for ncu captures (init, `steps` composite steps,
     moments): euler = the headline at n x n (default 2048, one launch per stage), euler_blocked =
-    the same through the temporally blocked 2D kernel (6 stages per launch), sw1d = the 1D workload
+    the same through the temporally blocked 2D kernel (`group` stages per launch), sw1d = the 1D workload
     at 2^20 cells, burgers2d[_blocked] = 2D Burgers entropic at n x n (default 4096), batched = 8 of
     the batched instances."""
     if case == "batched":
@@ -726,12 +727,12 @@ def profile_leg(torch, eslbm, inputs, stream, dev, case="euler", n=None, steps=2
     elif case.startswith("euler"):
         N = n or 2048
         cfg = eslbm.make_config(2, "euler", N, N, V=EULER_V, gamma=EULER_GAMMA, precision="fp32", omega_mode="fixed",
-                                blocking=6 if case.endswith("blocked") else True)
+                                blocking=group if case.endswith("blocked") else True)
         u0 = inputs.euler_vortex_2d(N, N)
     else:
         N = n or BURGERS_N
         cfg = eslbm.make_config(2, "burgers", N, N, V=BURGERS_V, precision="fp32", omega_mode="entropic",
-                                blocking=6 if case.endswith("blocked") else True)
+                                blocking=group if case.endswith("blocked") else True)
         u0 = inputs.burgers_2d(N, N)
     with torch.cuda.stream(stream):
         sim = eslbm.Simulation(cfg, stream=stream, device=dev)
@@ -766,7 +767,7 @@ def main():
         if args.leg == "precision" and args.n != EULER_N:
             kw = {"N": args.n}  # e.g. --leg precision --n 1048576: the 1D grid of the 1D workload
         if args.leg == "profile":
-            kw = {"case": args.case, "n": None if args.n == EULER_N else args.n}
+            kw = {"case": args.case, "n": None if args.n == EULER_N else args.n, "group": args.group}
         print(json.dumps(LEGS[args.leg](torch, eslbm, inputs, stream, dev, **kw)), flush=True)
         return
 

@@ -76,9 +76,7 @@ __device__ __forceinline__ void moments_target(const ParamsR<R> &P, const R *f, 
         du[m] = s[m] + P.cm[m];
         u[m] = P.ubar[m] + du[m];
     }
-    Sys::template equilibrium_dev<R>(P, du, u, tgt);
-#pragma unroll
-    for (int i = 0; i < Q * M; ++i) tgt[i] += P.rdev[i];
+    Sys::template equilibrium_dev<R>(P, du, u, tgt);  // includes rdev
 }
 
 // The kernel's constants in double precision, exactly as the kernel rounded them
