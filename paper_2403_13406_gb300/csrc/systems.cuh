@@ -32,18 +32,7 @@ template <> __host__ __device__ __forceinline__ float qdiv<float>(float a, float
 #endif
 }
 
-// The equilibria base + d and base - d of two opposite populations.  When |d| is a sizeable
-// fraction of |base| (8 |d| >= |base|) the two land in different binades, and rounded
-// independently they leave a bias in their sum that the relaxation turns into a steady drift of
-// the conserved moments (FP32: 3e-9 of the mass per cell-stage on 2D Burgers).  There the one away
-// from zero is rounded and the other is 2 base minus it, exact by Sterbenz's lemma when
-// |d| <= 3 |base|, so the pair sums to exactly 2 base.  For smaller |d| both share the binade of
-// base (or straddle one edge of it) and independent roundings are the symmetric choice: forcing
-// the exact sum there moves one member by up to an ulp and drifts more (1D shallow water at rest
-// on h = 2, where base = 1 sits on a binade edge).
-// a + b and a - b rounded once each and never merged with a product into a fused multiply-add, so
-// that the two members of a pair see the same rounded d whatever the compiler contracts around them
-// (contracting one member and not the other had left an asymmetric rounding in the pair's sum)
+// a + b and a - b rounded once each and never merged with a product into a fused multiply-add
 template <class R> __host__ __device__ __forceinline__ R add_rn(R a, R b)
 {
 #ifdef __CUDA_ARCH__
@@ -67,29 +56,15 @@ template <class R> __host__ __device__ __forceinline__ R sub_rn(R a, R b)
 #endif
 }
 
+// The equilibria base + d and base - d of two opposite populations (k and k + Q/2, same component),
+// both from the same rounded d, so that every kernel that inlines them (whatever it contracts
+// around them) computes the same values.  Their roundings need not sum to exactly 2 base: the
+// relaxation takes the deviation of the last population of each component from the others
+// (`deviations` in the kernels), so that this rounding never enters the conserved sums.
 template <class R> __host__ __device__ __forceinline__ void eq_pair(R base, R d, R &plus, R &minus)
 {
-    const R p = add_rn(base, d), m = sub_rn(base, d);
-    const R ab = base < R(0) ? -base : base, ad = d < R(0) ? -d : d;
-    if (R(8) * ad < ab) {
-        plus = p;
-        minus = m;
-        return;
-    }
-    const bool same = (base >= R(0)) == (d >= R(0));
-    const R big = same ? p : m;
-    const R other = sub_rn(add_rn(base, base), big);
-    plus = same ? big : other;
-    minus = same ? other : big;
-}
-
-// The pair of shifted-storage targets f^eq_k(u) - fbar_k = [f^eq_k(u) - f^eq_k(ubar)] + rdev_k for
-// planes k and kk (opposite populations, same component): the constant rdev of the pair enters as
-// its mean and half-difference before the pair is formed, so that the sum keeps the property above.
-template <class R> __device__ __forceinline__ void eq_pair_shifted(const ParamsR<R> &P, int k, int kk, R base, R d,
-                                                                   R &plus, R &minus)
-{
-    eq_pair<R>(base + R(0.5) * (P.rdev[k] + P.rdev[kk]), d + R(0.5) * (P.rdev[k] - P.rdev[kk]), plus, minus);
+    plus = add_rn(base, d);
+    minus = sub_rn(base, d);
 }
 
 // ---------------------------------------------------------------------------
@@ -124,8 +99,7 @@ template <int DIM, bool BURGERS> struct Scalar {
         if (DIM == 2) eq_pair<R>(base, phi1 * inv2V, feq[1], feq[3]);
     }
 
-    // The shifted-storage target f^eq_k(ubar + du) - fbar_k (u = ubar + du): the bracket
-    // f^eq_k(ubar + du) - f^eq_k(ubar) without cancellation, plus the constant rdev_k:
+    // f^eq_k(ubar + du) - f^eq_k(ubar) (u = ubar + du) without cancellation:
     // phi(u) - phi(ubar) = c du (u + ubar) / 2 (Burgers), a du (linear)
     template <class R> __device__ static void equilibrium_dev(const ParamsR<R> &P, const R *du, const R *u, R *fd)
     {
@@ -134,8 +108,8 @@ template <int DIM, bool BURGERS> struct Scalar {
 #pragma unroll
         for (int j = 0; j < DIM; ++j) dphi[j] = BURGERS ? P.c[j] * R(0.5) * du[0] * (u[0] + P.ubar[0]) : P.a[j] * du[0];
         const R base = du[0] / R(Q);
-        eq_pair_shifted<R>(P, 0, Q / 2, base, dphi[0] * inv2V, fd[0], fd[Q / 2]);
-        if (DIM == 2) eq_pair_shifted<R>(P, 1, 3, base, dphi[1] * inv2V, fd[1], fd[3]);
+        eq_pair<R>(base, dphi[0] * inv2V, fd[0], fd[Q / 2]);
+        if (DIM == 2) eq_pair<R>(base, dphi[1] * inv2V, fd[1], fd[3]);
     }
 
     // convexity of every s*_k at the equilibrium dual p = u
@@ -255,8 +229,7 @@ template <int DIM> struct ShallowWater {
         }
     }
 
-    // The shifted-storage target f^eq_k(ubar + du) - fbar_k (u = ubar + du): the bracket
-    // f^eq_k(ubar + du) - f^eq_k(ubar) without cancellation, plus the constant rdev_k: with
+    // f^eq_k(ubar + du) - f^eq_k(ubar) (u = ubar + du) without cancellation: with
     // v = q / h, dv = v - vbar = (dq - vbar dh) / h, q_a v_b - qbar_a vbar_b = dq_a v_b + qbar_a dv_b
     // and g h^2 / 2 - g hbar^2 / 2 = g dh (h + hbar) / 2
     // (P.aux[j] = vbar_j, the reference velocity)
@@ -286,8 +259,7 @@ template <int DIM> struct ShallowWater {
             const int j = Lattice<DIM>::axis(k);
 #pragma unroll
             for (int m = 0; m < M; ++m)
-                eq_pair_shifted<R>(P, k * M + m, (k + Q / 2) * M + m, du[m] / R(Q), dphi[j][m] * inv2V,
-                                   fd[k * M + m], fd[(k + Q / 2) * M + m]);
+                eq_pair<R>(du[m] / R(Q), dphi[j][m] * inv2V, fd[k * M + m], fd[(k + Q / 2) * M + m]);
         }
     }
 
@@ -526,8 +498,7 @@ struct Euler2 {
         }
     }
 
-    // The shifted-storage target f^eq_k(ubar + du) - fbar_k (u = ubar + du): the bracket
-    // f^eq_k(ubar + du) - f^eq_k(ubar) without cancellation, plus the constant rdev_k: with
+    // f^eq_k(ubar + du) - f^eq_k(ubar) (u = ubar + du) without cancellation: with
     // v = m / rho, dv = (dm - vbar drho) / rho, m_a v_b - mbar_a vbar_b = dm_a v_b + mbar_a dv_b,
     // dp = (gamma - 1)(dE - (dm.v + mbar.dv) / 2) and
     // v_a (E + p) - vbar_a (Ebar + pbar) = dv_a (E + p) + vbar_a (dE + dp)
@@ -550,8 +521,8 @@ struct Euler2 {
         const R inv2V = P.inv2V;
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            eq_pair_shifted<R>(P, 0 * 4 + m, 2 * 4 + m, du[m] * R(0.25), dphx[m] * inv2V, fd[0 * 4 + m], fd[2 * 4 + m]);
-            eq_pair_shifted<R>(P, 1 * 4 + m, 3 * 4 + m, du[m] * R(0.25), dphy[m] * inv2V, fd[1 * 4 + m], fd[3 * 4 + m]);
+            eq_pair<R>(du[m] * R(0.25), dphx[m] * inv2V, fd[0 * 4 + m], fd[2 * 4 + m]);
+            eq_pair<R>(du[m] * R(0.25), dphy[m] * inv2V, fd[1 * 4 + m], fd[3 * 4 + m]);
         }
     }
 

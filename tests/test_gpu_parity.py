@@ -401,12 +401,13 @@ def test_full_size_burgers2d_sampled():
     ("sw", 1, 1 << 16, dict(V=4.0, g=9.81), "entropic", 2000),
 ])
 def test_fp32_conservation_over_long_runs(system, dim, n, kw, mode, steps):
-    """The relaxation conserves the moments; in FP32 the equilibria of two opposite populations whose
-    roundings would land in different binades are built to sum to exactly 2 base, so what remains is
-    unbiased rounding: the mass after thousands of stages stays within a random walk of the FP32
-    rounding of the state (relative 1e-6), where independently rounded equilibria drifted by 1.4e-4
-    over 36 000 stages of 2D Burgers.  (Euler runs scheme III, the paper's Euler setting: the undamped
-    scheme I at omega = 2 does not stay finite over three crossings of the periodic domain at 384^2.)"""
+    """The relaxation conserves the moments: the deviation of the last population of each component is
+    minus the sum of the others, so the conserved totals move only by the rounding of the relaxed
+    values, unbiased: after thousands of stages the mass stays within a random walk of the FP32
+    rounding of the state (relative 1e-6), where deviations taken from independently rounded
+    equilibria drifted by 1.4e-4 over 36 000 stages of 2D Burgers.  (Euler runs scheme III, the
+    paper's Euler setting: in FP32 the undamped scheme I at omega = 2 does not stay finite over three
+    crossings of the periodic domain at 384^2, while FP64 does.)"""
     ny = n if dim == 2 else 1
     init = {"burgers": lambda: inputs.burgers_2d(n, n), "sw": lambda: (inputs.sw_random_2d(n, n, seed=4, h_amp=0.1)
                                                                       if dim == 2 else inputs.sw_sine_1d(n, 1.0, 0.1)),
