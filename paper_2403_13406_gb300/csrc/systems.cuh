@@ -318,6 +318,9 @@ template <int DIM> struct ShallowWater {
         R W, v[DIM], c[Q], f1[Q], d[Q][M];
         R rc[Q];      // 1 / c_k
         R rg0[Q];     // 1 / (f^eq_1 (W/(2c^2) - 1)): slope of the linearised equation in b
+        // FP32: the t-independent parts of the evaluations, once per cell: r(t) = t r1, the
+        // expansion b(t) = t beta1 + t^2 beta2 + ..., and the convergence scale |t| bs1 of b
+        R r1[Q], beta1[Q], beta2[Q], bs1[Q];
     };
 
     template <class R> __device__ static void prepare(const ParamsR<R> &P, const R *u, const R *delta, Ctx<R> &cx)
@@ -340,6 +343,21 @@ template <int DIM> struct ShallowWater {
             cx.rg0[k] = qdiv(R(1), cx.f1[k] * (R(0.5) * cx.W * cx.rc[k] * cx.rc[k] - R(1)));
 #pragma unroll
             for (int m = 0; m < M; ++m) cx.d[k][m] = delta[k * M + m];
+            if constexpr (sizeof(R) == 4) {
+                // linearised equation in b at b = 0: b = (r - lin) rg0, both terms linear in t
+                const R r1 = cx.d[k][1 + dax] - cx.v[dax] * cx.d[k][0];
+                const R lin1 = R(0.5) * sg * cx.W * cx.d[k][0] * cx.rc[k];
+                const R beta1 = (r1 - lin1) * cx.rg0[k];
+                // second-order term of b(t) from the expansion of G(b(t)) = 0: with
+                // K = 4 g V d_1 + sign W beta_1 the t^2 terms give
+                // beta_2 = (d_1 beta_1 - (2 W beta_1 + sign K) K / (16 g V c^2)) / (W^2/(8gVc) - f_1)
+                const R K = P.gV4 * cx.d[k][0] + sg * cx.W * beta1;
+                cx.r1[k] = r1;
+                cx.beta1[k] = beta1;
+                cx.beta2[k] = (cx.d[k][0] * beta1 -
+                               (R(2) * cx.W * beta1 + sg * K) * K * P.inv16gV * cx.rc[k] * cx.rc[k]) * cx.rg0[k];
+                cx.bs1[k] = (fabs(r1) + fabs(lin1)) * fabs(cx.rg0[k]);
+            }
         }
     }
 
@@ -364,27 +382,15 @@ template <int DIM> struct ShallowWater {
             const int dax = Lattice<DIM>::axis(k);
             const R sg = R(Lattice<DIM>::sign(k));
             h1[k] = t * cx.d[k][0];
-            const R hd = t * cx.d[k][1 + dax];
             f1p[k] = cx.f1[k] + h1[k];
             good &= f1p[k] > R(0);
-            r[k] = hd - cx.v[dax] * h1[k];
-            // linearised guess at b = 0; the magnitude of its two terms is the convergence
-            // scale of b (which itself can be far smaller when they cancel)
-            const R lin = R(0.5) * sg * W * h1[k] * cx.rc[k];
-            b[k] = (r[k] - lin) * cx.rg0[k];
-            bscale[k] = (fabs(r[k]) + fabs(lin)) * fabs(cx.rg0[k]);
             db[k] = R(0);
             if constexpr (FAST) {
-                const R beta1 = ((cx.d[k][1 + dax] - cx.v[dax] * cx.d[k][0]) -
-                                 R(0.5) * sg * W * cx.d[k][0] * cx.rc[k]) * cx.rg0[k];
+                const R beta1 = cx.beta1[k];
+                r[k] = t * cx.r1[k];
+                bscale[k] = fabs(t) * cx.bs1[k];
                 if constexpr (warm == 0) {
-                    // second-order guess b = t beta_1 + t^2 beta_2 from the expansion of G(b(t)) = 0:
-                    // with K = 4 g V d_1 + sign W beta_1 the t^2 terms give
-                    // beta_2 = (d_1 beta_1 - (2 W beta_1 + sign K) K / (16 g V c^2)) / (W^2/(8gVc) - f_1)
-                    const R K = gV4 * cx.d[k][0] + sg * W * beta1;
-                    const R beta2 = (cx.d[k][0] * beta1 -
-                                     (R(2) * W * beta1 + sg * K) * K * inv16gV * cx.rc[k] * cx.rc[k]) * cx.rg0[k];
-                    b[k] = t * (beta1 + t * beta2);
+                    b[k] = t * (beta1 + t * cx.beta2[k]);  // second-order guess
                 } else if constexpr (warm == 1) {
                     b[k] = bio[k] + R(2) * beta1;
                 } else {
@@ -392,6 +398,14 @@ template <int DIM> struct ShallowWater {
                     const R beta3 = R(0.5) * (bio[Q + k] - bio[k]) - beta1;
                     b[k] = t * (beta1 + t * (beta2 + t * beta3));
                 }
+            } else {
+                const R hd = t * cx.d[k][1 + dax];
+                r[k] = hd - cx.v[dax] * h1[k];
+                // linearised guess at b = 0; the magnitude of its two terms is the convergence
+                // scale of b (which itself can be far smaller when they cancel)
+                const R lin = R(0.5) * sg * W * h1[k] * cx.rc[k];
+                b[k] = (r[k] - lin) * cx.rg0[k];
+                bscale[k] = (fabs(r[k]) + fabs(lin)) * fabs(cx.rg0[k]);
             }
         }
         // one Newton step on G(b) = -b f'_1 - sign dW (2W - dW)/(16 g V) - r for population k

@@ -50,7 +50,11 @@ def test_dam_break_entropy_decreases(precision, uref):
     if precision != "fp32":
         assert d["entropy_excess_max"] <= 64 * 2.3e-16  # FP64 evaluation of the entropy difference
     assert 1.0 <= d["omega_min"] and d["omega_max"] <= 4.0  # fallbacks (omega = 1) are allowed at the fronts
-    assert t[0] < t0[0]  # the shocks dissipate entropy
+    # relaxing at the root of eq. variableOmegaProblem keeps each cell's microscopic entropy (lowered
+    # only by the chord and by fallbacks), so the total Sigma(f) may stay at its initial value to
+    # rounding (it does in FP64); the entropy of the moments, S(u) <= Sigma(f), falls below its
+    # initial value at the shocks
+    assert t[1] < t0[1]
     # conservation of h and hu (exact up to the reductions' rounding in FP64, FP32 state rounding)
     ctol = 1e-12 if precision == "fp64" else 1e-6
     assert abs(t[2] - t0[2]) <= ctol * abs(t0[2])
