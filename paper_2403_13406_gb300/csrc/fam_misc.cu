@@ -281,33 +281,35 @@ int device_sms()
     return sms;
 }
 
-bool plan_step2d(int64_t nx, int64_t ny, int planes, int elem, int sms, const StageList &sl, Plan2d &pl)
+// One candidate plan with R rows per tick: the lags in ticks, the ring that keeps every block until its
+// last reader, the widest strip the shared memory allows and the tick's items.
+static bool plan_rows(int64_t nx, int64_t ny, int planes, int elem, int sms, const StageList &sl, int R,
+                      int items_cap, Plan2d &pl)
 {
-    if (!stage_list_ok(sl) || sl.n > kStep2dMaxStages || planes < 1 || (elem != 4 && elem != 8)) return false;
     const int V4 = 16 / elem;
-    if (nx % V4) return false;
     const int H = sl.halo;
-    // lags of the stages behind the load, and the ring that keeps every slot until its last reader
-    int lag = 0, acc = 0, E = 0;
+    int L = 0, acc = 0, EB = 0, m = 0;
     int64_t items_margin = 0;
-    int m = 0;
     for (int j = 0; j < sl.n; ++j) {
         const int s = sl.shift[j], as = s < 0 ? -s : s;
-        lag += as + (j > 0 ? 1 : 0);
+        L = (j > 0 ? L + 1 : 0) + (as + R - 1) / R;
         acc += s;
         m += as;
-        E = std::max(E, lag + (acc < 0 ? -acc : acc));
+        const int aa = acc < 0 ? -acc : acc;
+        EB = std::max(EB, L + (aa + R - 1) / R);
         items_margin += 2 * (H - m);
     }
-    pl.prefetch = kStep2dPrefetch;
-    pl.ring = E + pl.prefetch;
+    pl.rpt = R;
+    pl.prefetch = (kStep2dPrefetch + R - 1) / R;
+    const int ringB = EB + pl.prefetch;
+    pl.ring = ringB * R;
     if (pl.ring > kStep2dMaxRing) return false;
     pl.hl = (H + V4 - 1) / V4 * V4;
     const int64_t budget = kStep2dSmemBudget - kStep2dBarBytes;
     const int wx_max = (int)(budget / ((int64_t)pl.ring * planes * elem)) / V4 * V4;
     const int tx_max = wx_max - 2 * pl.hl;
-    // a tick's items (about n tx) must fit the slots of the smallest block
-    const int tx_cap = (int)std::min<int64_t>(tx_max, (kStep2dMaxItems - items_margin) / sl.n / V4 * V4);
+    // a tick's items (about R n tx) within items_cap (at most the slots of the smallest block)
+    const int tx_cap = (int)std::min<int64_t>(tx_max, (items_cap / R - items_margin) / sl.n / V4 * V4);
     if (tx_cap < std::max(4 * V4, pl.hl)) return false;
     // strips as wide as the window allows, evened out over the row
     int64_t nstrips = (nx + tx_cap - 1) / tx_cap;
@@ -316,7 +318,8 @@ bool plan_step2d(int64_t nx, int64_t ny, int planes, int elem, int sms, const St
     nstrips = (nx + pl.tx - 1) / pl.tx;
     pl.nstrips = (int)nstrips;
     pl.wx = pl.tx + 2 * pl.hl;
-    // rows per block: the time is (waves of kStep2dBlocksPerSm blocks per SM) x (ticks of a block)
+    // rows per block: the time is (waves of kStep2dBlocksPerSm blocks per SM) x (rows a block sweeps,
+    // with the pipeline's fill and drain)
     static const int cand[] = {32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096, 8192};
     double best = 0.0;
     pl.ly = 0;
@@ -325,7 +328,7 @@ bool plan_step2d(int64_t nx, int64_t ny, int planes, int elem, int sms, const St
         const int64_t nsegs = (ny + lye - 1) / lye;
         const int64_t blocks = nstrips * nsegs;
         const int64_t waves = (blocks + (int64_t)sms * kStep2dBlocksPerSm - 1) / ((int64_t)sms * kStep2dBlocksPerSm);
-        const double cost = (double)waves * (double)(lye + H + lag);
+        const double cost = (double)waves * (double)(lye + 2 * H + R * L);
         if (pl.ly == 0 || cost < best) {
             best = cost;
             pl.ly = lye;
@@ -334,9 +337,33 @@ bool plan_step2d(int64_t nx, int64_t ny, int planes, int elem, int sms, const St
         if (ly >= ny) break;
     }
     if ((int64_t)pl.nstrips * pl.nsegs > 0x7fffffffLL) return false;
-    pl.items = (int)((int64_t)sl.n * pl.tx + items_margin);
+    pl.items = (int)((int64_t)R * (sl.n * (int64_t)pl.tx + items_margin));
     pl.smem = (size_t)kStep2dBarBytes + (size_t)pl.ring * planes * pl.wx * elem;
     return pl.smem <= (size_t)kStep2dSmemBudget;
+}
+
+bool plan_step2d(int64_t nx, int64_t ny, int planes, int elem, int sms, const StageList &sl, int consumers, Plan2d &pl)
+{
+    if (!stage_list_ok(sl) || sl.n > kStep2dMaxStages || planes < 1 || (elem != 4 && elem != 8) || consumers < 32)
+        return false;
+    if (nx % (16 / elem)) return false;
+    // Rows per tick: the fewest that give every consumer a cell each tick, with the strip narrowed to
+    // one cell per consumer when more rows were needed (more rows than needed only grow the ring and
+    // narrow the strips); the most that fit when none does.  One row per tick keeps the widest strip
+    // and gives the consumers several cells each where the tick holds more cells than consumers.
+    bool any = false;
+    for (int R : {1, 2, 4}) {
+        Plan2d c;
+        if (!plan_rows(nx, ny, planes, elem, sms, sl, R, kStep2dMaxItems, c)) continue;
+        pl = c;
+        any = true;
+        if (c.items >= consumers) {
+            Plan2d d;
+            if (R > 1 && plan_rows(nx, ny, planes, elem, sms, sl, R, consumers, d)) pl = d;
+            break;
+        }
+    }
+    return any;
 }
 
 cudaError_t batch_adjoint_sw2(bool, int, const BatchAdjointLaunch &);
