@@ -65,7 +65,7 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="headline only (no other workloads, no CPU baseline)")
     p.add_argument("--leg", default=None,
                    choices=["sw1d", "burgers2d", "riemann", "batched", "precision", "accuracy", "adjoint", "cpu",
-                            "blocked2d", "profile"],
+                            "blocked2d", "profile", "batched_accuracy"],
                    help="run one secondary measurement alone and print its JSON")
     p.add_argument("--batch-count", type=int, default=64, help="instances of the batched leg")
     p.add_argument("--group", type=int, default=6, help="profile leg: stages per blocked 2D launch")
@@ -687,6 +687,79 @@ def batch_leg(torch, eslbm, inputs, stream, dev, count=64, steps=BATCH_STEPS, K=
     return {"batched": out}
 
 
+def batched_accuracy_leg(torch, eslbm, inputs, stream, dev, count=8, base=(32, 128), levels=(1, 2, 4), ref_level=8,
+                         n0=4, targets=(1e-4, 1e-5, 1e-6)):
+    """Time to a stated L2 error in the batched form: `count` 2D shallow-water instances of uneven seeded
+    sizes (base range, scaled by each refinement level) with the 8-mode Fourier depth data of the batched
+    workload, advanced as one batch in FP32 by the composite scheme (entropic omega, shifted storage,
+    one cooperative launch per composite step from CUDA graphs), against the same batch in FP64 by the
+    plain second-order scheme R T (omega = 2, 24 plain steps per composite step: the same final time on
+    every level and instance).  Level l runs l n0 composite steps.  The error of h is the relative L2
+    norm over all instances against FP64 composite solutions at `ref_level` times the base resolution,
+    sampled at the coarse cells.  Times are CUDA-event times of the steps alone."""
+    rng_sizes = [(max(4, a // 4 * 4), max(4, b // 4 * 4)) for a, b in inputs.batched_sizes(count, *base)]
+    refs = []
+    for i, (nx, ny) in enumerate(rng_sizes):
+        c64 = eslbm.make_config(2, "sw", nx * ref_level, ny * ref_level, V=BATCH_V, g=G, precision="fp64",
+                                omega_mode="entropic")
+        with torch.cuda.stream(stream):
+            s64 = eslbm.Simulation(c64, stream=stream, device=dev)
+            s64.use_graph(True)
+            s64.init_equilibrium(torch.from_numpy(inputs.sw_fourier_2d(nx * ref_level, ny * ref_level,
+                                                                       seed=1000 + i)).to(dev))
+            s64.step(n0 * ref_level)
+            refs.append(s64.moments()[0].cpu().numpy())
+            s64.close()
+
+    def run(level, prec, scheme):
+        sizes = [(nx * level, ny * level) for nx, ny in rng_sizes]
+        plain = scheme == "plain"
+        cfg = eslbm.make_config(2, "sw", 1, 1, V=BATCH_V, g=G, precision=prec,
+                                omega_mode="fixed" if plain else "entropic", omega=2.0, scheme=scheme,
+                                u_ref=None if plain else (1.0, 0.0, 0.0))
+        steps = n0 * level * (24 if plain else 1)
+        with torch.cuda.stream(stream):
+            b = eslbm.Batch(cfg, sizes, stream=stream, device=dev)
+            u0 = b.pack([inputs.sw_fourier_2d(nx, ny, seed=1000 + i) for i, (nx, ny) in enumerate(sizes)])
+            b.use_graph(True)
+            b.init_equilibrium(u0)
+            b.step(min(steps, 24))  # warm-up: captures the graphs
+            b.init_equilibrium(u0)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            hs = [m[0].cpu().numpy() for m in b.moments()]
+            cells = b.total_cells
+            b.close()
+        f = ref_level // level
+        num = sum(float(np.sum((h - r[::f, ::f]) ** 2)) for h, r in zip(hs, refs))
+        den = sum(float(np.sum(r[::f, ::f] ** 2)) for r in refs)
+        return {"rel_l2": (num / den) ** 0.5, "ms": ms, "cells": cells, "steps": steps}
+
+    rows = []
+    for level in levels:
+        rows.append({"level": level, "fp32_batched_composite": run(level, "fp32", "I"),
+                     "fp64_batched_plain": run(level, "fp64", "plain")})
+    best = {}
+    for eps in targets:
+        pick = {}
+        for name in ("fp32_batched_composite", "fp64_batched_plain"):
+            ok = [r for r in rows if r[name]["rel_l2"] <= eps]
+            pick[name] = {"level": ok[0]["level"], **ok[0][name]} if ok else None
+        if pick["fp32_batched_composite"] and pick["fp64_batched_plain"]:
+            pick["speedup_fp32_batched"] = pick["fp64_batched_plain"]["ms"] / pick["fp32_batched_composite"]["ms"]
+        best["%g" % eps] = pick
+    return {"batched_time_to_accuracy": {
+        "instances": count, "base_sizes": "seeded uniform nx, ny in [%d, %d], multiples of 4" % base,
+        "levels": list(levels), "composite_steps_at_level_1": n0,
+        "reference": "fp64 composite per instance at %d x the base resolution" % ref_level,
+        "sweep": rows, "at_target_rel_l2": best}}
+
+
 def cpu_leg():
     """The FP64 oracle on the host cores: single-threaded and OpenMP over every core, on bounded samples
     of the headline and of the 1D workload (rates in site updates per second)."""
@@ -745,6 +818,7 @@ def profile_leg(torch, eslbm, inputs, stream, dev, case="euler", n=None, steps=2
 
 
 LEGS = {"sw1d": sw1d_leg, "burgers2d": burgers2d_leg, "riemann": riemann_leg, "batched": batch_leg,
+        "batched_accuracy": batched_accuracy_leg,
         "blocked2d": blocked2d_leg, "profile": profile_leg,
         "precision": precision_leg, "accuracy": accuracy_leg, "adjoint": adjoint_leg}
 
@@ -788,8 +862,11 @@ def main():
     extras, cpu = {}, None
     if not args.no_extras and rank == 0:
         for leg in (sw1d_leg, burgers2d_leg, riemann_leg, blocked2d_leg, precision_leg, fp32_vs_fp64_leg,
-                    accuracy_leg, adjoint_leg):
-            extras.update(leg(torch, eslbm, inputs, stream, dev))
+                    accuracy_leg, batched_accuracy_leg, adjoint_leg):
+            try:
+                extras.update(leg(torch, eslbm, inputs, stream, dev))
+            except Exception as e:  # a failing extra is reported, and does not take the headline line with it
+                extras[leg.__name__] = {"error": "%s: %s" % (type(e).__name__, str(e)[:300])}
         extras.update(batch_leg(torch, eslbm, inputs, stream, dev, count=args.batch_count, grad_steps=100,
                                 K=10))
     if rank == 0 and world == 1 and not args.no_extras:

@@ -131,6 +131,12 @@ struct StageList {
 #ifndef ESLBM_STEP2D_PREFETCH
 #define ESLBM_STEP2D_PREFETCH 3
 #endif
+#ifndef ESLBM_STEP2D_ROWS
+#define ESLBM_STEP2D_ROWS 1
+#endif
+#ifndef ESLBM_STEP2D_NARROW
+#define ESLBM_STEP2D_NARROW 0
+#endif
 #ifndef ESLBM_STEP2D_THREADS
 #define ESLBM_STEP2D_THREADS 768
 #endif
@@ -139,6 +145,8 @@ constexpr int kStep2dSlots = 8;                                   // items (stag
 constexpr int kStep2dMaxItems = kStep2dSlots * (256 - 32);        // items of a tick (smallest block: 256)
 constexpr int kStep2dBlocksPerSm = ESLBM_STEP2D_BLOCKS_PER_SM;  // resident blocks per SM (shared memory split)
 constexpr int kStep2dPrefetch = ESLBM_STEP2D_PREFETCH;          // window rows loaded ahead of use (at least)
+constexpr int kStep2dRowsPerTick = ESLBM_STEP2D_ROWS;  // rows a stage advances per tick (1, 2 or 4)
+constexpr bool kStep2dNarrow = ESLBM_STEP2D_NARROW;     // narrow the strip to one cell per consumer when rows > 1
 constexpr int kStep2dMaxStages = 32;
 constexpr int kStep2dMaxRing = 64;
 constexpr int kStep2dBarBytes = 8 * kStep2dMaxRing;
