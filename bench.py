@@ -224,6 +224,7 @@ def headline_config(n, steps):
     return {"workload": "euler2d_d2q4_vortex_n%d_steps%d" % (n, steps), "system": "euler", "lattice": "D2Q4",
             "nx": n, "ny": n, "M": 4, "V": EULER_V, "gamma": EULER_GAMMA, "scheme": "I", "omega": "fixed 2",
             "composite_steps": steps, "stages_per_step": 18, "precision": "fp32", "storage": "plain",
+            "blocking": "auto: temporally blocked 2D kernel, 2 stages per launch (9 launches per step)",
             "initial_data": "isentropic vortex, strength 5, rho = p = 1, velocity (1, 1), on [0, 10]^2",
             "l2": "inputs larger than L2 (4.3 GB per state buffer); no flush needed"}
 

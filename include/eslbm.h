@@ -71,8 +71,10 @@ enum { ESLBM_LINEAR = 0, ESLBM_BURGERS = 1, ESLBM_SHALLOW_WATER = 2, ESLBM_EULER
    t.  With a fixed omega FP32_MIXED is FP32. */
 enum { ESLBM_FP32 = 0, ESLBM_FP64 = 1, ESLBM_FP32_MIXED = 2 };
 /* Temporal blocking (eslbm_config.blocking): AUTO runs the fastest measured path
-   -- 1D: every step in one launch from shared memory; 2D: one launch per fused
-   stage.  OFF runs one launch per fused stage in 1D too (the same per-cell
+   -- 1D: every step in one launch from shared memory; 2D: the temporally blocked
+   2D kernel two stages a launch for Euler (16 planes) in FP32 with a fixed omega,
+   one launch per fused stage otherwise.  OFF runs one launch per fused stage in
+   1D and 2D (the same per-cell
    arithmetic; used to cross-check the blocked kernels).  A value n in [2, 32]
    runs the temporally blocked 2D kernel where rows start on 16-byte boundaries
    (nx a multiple of 4 in FP32 and FP32_MIXED, of 2 in FP64), at most n stages

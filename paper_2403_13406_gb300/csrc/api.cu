@@ -64,22 +64,34 @@ int64_t fused_group_of(int64_t stages_per_step)
     return stages_per_step >= 16 ? 1 : std::max<int64_t>(1, 24 / stages_per_step);
 }
 
-// most stages of one launch of the temporally blocked 2D kernel (the configuration's limit)
-int max_group2d_of(const eslbm_config &c, int64_t) { return c.blocking; }
-
-// 2D runs take the temporally blocked kernel when asked for (blocking >= 2) and rows start on
-// 16-byte boundaries; by default one launch per stage, which measured faster on GB300 (the
-// stage kernel streams at the HBM roofline, the blocked one is bound by its per-row barrier).
-bool blocked2d_of(const eslbm_config &c)
+// Most stages of one launch of the temporally blocked 2D kernel: the configuration's limit, or with
+// AUTO the fastest measured on GB300 -- two stages a launch for the 16-plane Euler state in FP32 with a
+// fixed omega (3.28e9 against 3.03e9 site updates/s at 8192^2: the per-stage kernel is at the HBM
+// roofline, the blocked one halves the traffic and is bound by instruction issue), one launch per
+// stage otherwise (the blocked kernel was slower for the 4-plane states and for the entropic
+// relaxations, whose arithmetic bounds both paths).
+int max_group2d_of(const eslbm_config &c, int64_t planes)
 {
-    return c.dim == 2 && c.blocking >= 2 && c.nx % (c.precision == ESLBM_FP64 ? 2 : 4) == 0;
+    if (c.blocking >= 2) return c.blocking;
+    if (c.blocking == ESLBM_BLOCKING_AUTO && c.dim == 2 && planes >= 16 && c.omega_mode == ESLBM_OMEGA_FIXED &&
+        c.precision != ESLBM_FP64)
+        return 2;
+    return 0;
+}
+
+// 2D runs take the temporally blocked kernel when it applies (above) and rows start on 16-byte
+// boundaries, else one launch per stage.
+bool blocked2d_of(const eslbm_config &c, int64_t planes)
+{
+    return c.dim == 2 && max_group2d_of(c, planes) >= 2 && c.nx % (c.precision == ESLBM_FP64 ? 2 : 4) == 0;
 }
 
 // Stages one launch may run: the record buffer of the diagnostics holds that many.
 int64_t max_launch_stages(const eslbm_config &c, int64_t stages_per_step, int64_t planes)
 {
     if (c.dim == 1 && c.blocking != ESLBM_BLOCKING_OFF) return stages_per_step * fused_group_of(stages_per_step);
-    if (blocked2d_of(c)) return std::min<int64_t>(stages_per_step, std::min(max_group2d_of(c, planes), kStep2dMaxStages));
+    if (blocked2d_of(c, planes))
+        return std::min<int64_t>(stages_per_step, std::min(max_group2d_of(c, planes), kStep2dMaxStages));
     return 1;
 }
 
@@ -254,7 +266,7 @@ eslbm_status run_fused(eslbm_handle *h, int64_t steps)
 
 // 2D runs use the temporally blocked 2D kernel (unless blocking is off) when rows start on
 // 16-byte boundaries: the stages of a step in groups, each group one launch.
-bool blocked2d_path(const eslbm_handle *h) { return blocked2d_of(h->cfg); }
+bool blocked2d_path(const eslbm_handle *h) { return blocked2d_of(h->cfg, h->sz.planes); }
 
 int max_group2d(const eslbm_handle *h) { return max_group2d_of(h->cfg, h->sz.planes); }
 
@@ -614,11 +626,13 @@ eslbm_status eslbm_query(const eslbm_config *cfg, eslbm_sizes *out)
     z.launches_per_step = (double)stages;
     if (cfg->dim == 1 && cfg->blocking != ESLBM_BLOCKING_OFF) {
         z.launches_per_step = 1.0 / (double)fused_group_of(stages);
-    } else if (blocked2d_of(*cfg)) {
-        eslbm_handle probe;  // the grouping needs the configuration, sizes and operator list only
+    } else if (blocked2d_of(*cfg, z.planes)) {
+        eslbm_handle probe;  // the grouping needs the configuration, sizes, family, omega mode and operator list
         probe.cfg = *cfg;
         probe.sz = z;
         probe.fp64 = cfg->precision == ESLBM_FP64;
+        probe.family = family_of(*cfg);
+        probe.om = omega_mode_of(*cfg);
         probe.ops = scheme_ops(cfg->scheme, cfg->kappa);
         int64_t pend = 0;
         for (const Op &op : probe.ops)  // the trailing shift that a step leaves pending
