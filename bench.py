@@ -149,14 +149,28 @@ def aggregate(total_ms, units_per_rank, dist=None, device=None):
     return world * units_per_rank / (total_ms * 1e-3), total_ms
 
 
-def hbm_roofline(bytes_per_site_update, site_updates, seconds, kernel, launches, extra=None):
+# DRAM bytes (read + write) per launch of the dominant kernels, from the ncu captures summarised under
+# profiles/ (at a smaller size where noted, scaled by the cells a launch processes)
+TRAFFIC = {
+    "k_step2d_euler_8192_g2": (8.18e9, "profiles/k_step2d_euler_n2048_g2.md: 511 MB at 2048^2, x 16"),
+    "k_stage_bulk_euler_8192": (7.70e9, "profiles/k_stage_bulk_euler_n2048_fp32_fixed.md: 481 MB at 2048^2, x 16"),
+    "k_step1d_sw1d_2^20": (16.8e6, "profiles/k_step1d_sw1d_n1048576_fp32_entropic.md (the writes stay in L2)"),
+    "k_batch_step_sw2d_64": (47.0e9, "profiles/k_batch_step_sw2d_8inst_fp32_entropic.md: 7.18 GB for 4.12 M cells, "
+                                     "x 26.99 M / 4.12 M"),
+}
+
+
+def hbm_roofline(bytes_per_site_update, site_updates, seconds, kernel, launches, extra=None, traffic=None):
     """Per-stage traffic model of the path (every distribution read and written once per fused
     stage, 2 q M b bytes per cell-stage, 18 cell-stages per site update) over the dominant kernel's
-    launches, timed back to back on one stream with CUDA events."""
+    launches, timed back to back on one stream with CUDA events; `traffic` names the ncu-measured DRAM
+    bytes per launch (TRAFFIC) where the kernel was captured."""
     peak, kind = peaks()
     achieved = bytes_per_site_update * site_updates / seconds / 1e9
     r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-         "traffic": None, "model": "per-stage: 18 x 2 q M b bytes per site update",
+         "traffic": TRAFFIC[traffic][0] if traffic else None,
+         "traffic_source": TRAFFIC[traffic][1] if traffic else None,
+         "model": "per-stage: 18 x 2 q M b bytes per site update",
          "bytes_per_site_update": bytes_per_site_update, "peak_source": kind, "kernel": kernel,
          "launches": launches, "launch_us": seconds / max(launches, 1) * 1e6}
     if extra:
@@ -281,9 +295,14 @@ def headline(torch, eslbm, inputs, stream, dev, args, world, dist, local):
     bytes_su = 18 * 2 * int(sz.planes) * 4
     kernel = "k_step2d<Euler2, float, fixed> (temporally blocked, %g launches per step)" % launches_step \
         if launches_step < 18 else "k_stage_bulk<Euler2, float, fixed> (one launch per stage)"
+    traffic = None
+    if n == 8192:
+        traffic = "k_step2d_euler_8192_g2" if launches_step == 9 else \
+            ("k_stage_bulk_euler_8192" if launches_step == 18 else None)
     roof = hbm_roofline(bytes_su, n * n * n_steps, statistics.mean(kern_ms) * 1e-3, kernel,
                         int(round(launches_step * n_steps)),
-                        {"site_updates_per_s_kernel": n * n * n_steps / (statistics.mean(kern_ms) * 1e-3)})
+                        {"site_updates_per_s_kernel": n * n * n_steps / (statistics.mean(kern_ms) * 1e-3)},
+                        traffic=traffic)
     with torch.cuda.stream(stream):
         # conservation over the run (FP64 totals) and the vortex after n steps: finite state
         t0 = np.asarray(sim.totals())
@@ -364,7 +383,8 @@ def sw1d_leg(torch, eslbm, inputs, stream, dev):
     roof = hbm_roofline(18 * 2 * planes * 4, N * n_steps, s, "k_step1d<ShallowWater<1>, float, entropic>",
                         n_steps, {"alu_view": {"achieved_tflops": flops, "peak_tflops": FP32_PEAK_TFLOPS,
                                                "frac": flops / FP32_PEAK_TFLOPS,
-                                               "flops_per_cell_stage": SW_FLOPS_PER_CELL_STAGE}})
+                                               "flops_per_cell_stage": SW_FLOPS_PER_CELL_STAGE}},
+                        traffic="k_step1d_sw1d_2^20" if N == 1 << 20 else None)
     return {"sw1d": {"workload": "sw1d_d1q2_entropic_n%d_t%g" % (N, SW_T), "N": N, "V": SW_V, "g": G,
                      "t_final": n_steps * 24.0 / N / SW_V, "composite_steps": n_steps, "ms": ms,
                      "site_updates_per_s": N * n_steps / s, "roofline": roof, "fallbacks": fb,
@@ -439,7 +459,9 @@ def riemann_leg(torch, eslbm, inputs, stream, dev, omega=1.98):
     return {"euler_riemann": {"workload": "euler2d_d2q4_riemann_n%d_steps%d_schemeIII" % (n, RIEMANN_STEPS),
                               "omega": omega, "ms": ms, "site_updates_per_s": n * n * RIEMANN_STEPS / s,
                               "roofline": hbm_roofline(27 * 2 * 16 * 4, n * n * RIEMANN_STEPS, s,
-                                                       "k_stage_bulk<Euler2, float, fixed>", int(round(lps * RIEMANN_STEPS)),
+                                                       ("k_step2d<Euler2, float, fixed> (temporally blocked, %g launches "
+                                                        "per step)" % lps) if lps < 27 else "k_stage_bulk<Euler2, float, fixed>",
+                                                       int(round(lps * RIEMANN_STEPS)),
                                                        {"model": "per-stage: 27 x 2 q M b bytes per step (scheme III)"}),
                               "state": rows}}
 
@@ -670,7 +692,8 @@ def batch_leg(torch, eslbm, inputs, stream, dev, count=64, steps=BATCH_STEPS, K=
         out = {"instances": count, "total_cells": cells, "sizes": "seeded uniform nx, ny in [256, 1024]",
                "steps": steps, "ms": ms, "site_updates_per_s": cells * steps / (ms * 1e-3),
                "roofline": hbm_roofline(18 * 2 * 12 * 4, cells * steps, ms * 1e-3,
-                                        "k_batch_step<ShallowWater<2>, float, entropic>", steps),
+                                        "k_batch_step<ShallowWater<2>, float, entropic>", steps,
+                                        traffic="k_batch_step_sw2d_64" if count == 64 else None),
                "schedule": {"segment": sched[0], "blocks_per_sm": sched[1], "order": sched[2]},
                "tune_s": tune_s, "cuda_graph": True, "fallbacks": fallbacks, "V": BATCH_V,
                "storage": "fp32, shifted, u_ref = (1, 0, 0)",
