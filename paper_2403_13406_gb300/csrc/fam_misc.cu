@@ -347,14 +347,12 @@ bool plan_step2d(int64_t nx, int64_t ny, int planes, int elem, int sms, const St
     if (!stage_list_ok(sl) || sl.n > kStep2dMaxStages || planes < 1 || (elem != 4 && elem != 8) || consumers < 32)
         return false;
     if (nx % (16 / elem)) return false;
-    // Rows per tick: kStep2dRowsPerTick where it fits, else one.  One row per tick measured fastest on
-    // GB300 (Euler 8192^2, two stages a launch: 204 ms for ten steps against 269 ms with two rows a
-    // tick and the strip narrowed to one cell per consumer, where the consumers then waited on the
-    // rows' copies); more rows per tick remain available for experiments.
-    if (kStep2dRowsPerTick > 1 &&
-        plan_rows(nx, ny, planes, elem, sms, sl, kStep2dRowsPerTick, kStep2dNarrow ? consumers : kStep2dMaxItems, pl))
-        return true;
-    return plan_rows(nx, ny, planes, elem, sms, sl, 1, kStep2dMaxItems, pl);
+    // Rows per tick: kStep2dRowsPerTick, a constant of the kernel.  One row per tick measured fastest on
+    // GB300 (Euler 8192^2, two stages a launch: 204 ms for ten steps against 231 ms with two rows a
+    // tick, and 269 ms with two rows and the strip narrowed to one cell per consumer, where the
+    // consumers then waited on the rows' copies); more rows per tick remain a build option.
+    return plan_rows(nx, ny, planes, elem, sms, sl, kStep2dRowsPerTick,
+                     (kStep2dRowsPerTick > 1 && kStep2dNarrow) ? consumers : kStep2dMaxItems, pl);
 }
 
 cudaError_t batch_adjoint_sw2(bool, int, const BatchAdjointLaunch &);

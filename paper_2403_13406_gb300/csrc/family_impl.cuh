@@ -271,7 +271,7 @@ cudaError_t step2d_one(const Step2dLaunch &L)
         if (e != cudaSuccess) return e;
         attr[d].store(1);
     }
-    if (pl.rpt < 1 || pl.ring % pl.rpt) return cudaErrorInvalidValue;
+    if (pl.rpt != kStep2dRowsPerTick || pl.ring % pl.rpt) return cudaErrorInvalidValue;
     Step2dArgs<R> a{(const R *)L.fin, (R *)L.fout, L.nx, L.ny, L.ncell, pl.tx, pl.ly, pl.hl, pl.wx, pl.ring,
                     pl.prefetch, pl.nstrips, pl.rpt, L.cnt};
     const unsigned grid = (unsigned)((int64_t)pl.nstrips * pl.nsegs);

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(Step2dThreads<Sys, R, OM>::value, kStep2dBlock
     const int wx = tx + 2 * a.hl;  // this block's window width (<= a.wx)
     const int nrows = ly + 2 * H;  // window rows
     const int rowstride = NP * a.wx;
-    const int Rt = a.rpt;                       // rows per tick
+    constexpr int Rt = kStep2dRowsPerTick;      // rows per tick (the launcher checks a.rpt)
     const int nblk = (nrows + Rt - 1) / Rt;     // blocks of rows of the window
     const int ringB = a.ring / Rt;              // blocks in the ring (one mbarrier each)
     if (threadIdx.x == 0) {
@@ -110,7 +110,9 @@ __global__ void __launch_bounds__(Step2dThreads<Sys, R, OM>::value, kStep2dBlock
     }
     __syncthreads();
     const int items = sOff[G];
-    const int ticks = nblk + sLag[G - 1];
+    // the last stage's last row, nrows - H - 1, is in block (nrows - H - 1) / Rt, relaxed in tick
+    // that + L_G
+    const int ticks = (nrows - H - 1) / Rt + sLag[G - 1] + 1;
     int64_t gx0 = (x0 - a.hl) % a.nx;
     if (gx0 < 0) gx0 += a.nx;
     // r mod ring for 0 <= r < 2^16 and ring <= 64: (r * ceil(2^22 / ring)) >> 22 is the exact quotient
