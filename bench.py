@@ -152,7 +152,7 @@ def aggregate(total_ms, units_per_rank, dist=None, device=None):
 # DRAM bytes (read + write) per launch of the dominant kernels, from the ncu captures summarised under
 # profiles/ (at a smaller size where noted, scaled by the cells a launch processes)
 TRAFFIC = {
-    "k_step2d_euler_8192_g2": (8.18e9, "profiles/k_step2d_euler_n2048_g2.md: 511 MB at 2048^2, x 16"),
+    "k_step2d_euler_8192_g2": (8.20e9, "profiles/k_step2d_euler_n2048_g2.md: 513 MB at 2048^2, x 16"),
     "k_stage_bulk_euler_8192": (7.70e9, "profiles/k_stage_bulk_euler_n2048_fp32_fixed.md: 481 MB at 2048^2, x 16"),
     "k_step1d_sw1d_2^20": (16.8e6, "profiles/k_step1d_sw1d_n1048576_fp32_entropic.md (the writes stay in L2)"),
     "k_batch_step_sw2d_64": (47.0e9, "profiles/k_batch_step_sw2d_8inst_fp32_entropic.md: 7.18 GB for 4.12 M cells, "
@@ -479,7 +479,7 @@ def blocked2d_leg(torch, eslbm, inputs, stream, dev, steps=10):
               lambda n: inputs.burgers_2d(n, n), 16))
     for name, system, n, kw, mode, init, bpc in cases:
         row = {}
-        for label, blocking in (("per_stage", True), ("blocked_6", 6), ("blocked_3", 3)):
+        for label, blocking in (("per_stage", False), ("blocked_2", 2), ("blocked_3", 3), ("blocked_6", 6)):
             cfg = eslbm.make_config(2, system, n, n, precision="fp32", omega_mode=mode, blocking=blocking, **kw)
             u0 = torch.from_numpy(init(n)).to(dev)
             with torch.cuda.stream(stream):
@@ -495,7 +495,9 @@ def blocked2d_leg(torch, eslbm, inputs, stream, dev, steps=10):
             peak, _ = peaks()
             row[label] = {"site_updates_per_s": sps, "launches_per_step": lps,
                           "per_stage_model_frac": sps * 18 * 2 * bpc / 1e9 / peak}
-        row["blocked_6_over_per_stage"] = row["blocked_6"]["site_updates_per_s"] / row["per_stage"]["site_updates_per_s"]
+        for g in (2, 3, 6):
+            row["blocked_%d_over_per_stage" % g] = (row["blocked_%d" % g]["site_updates_per_s"] /
+                                                    row["per_stage"]["site_updates_per_s"])
         out[name] = row
     return {"blocked2d": out}
 

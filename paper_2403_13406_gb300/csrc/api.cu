@@ -296,8 +296,6 @@ bool step_groups2d(const eslbm_handle *h, int64_t pending, std::vector<Group2d> 
     const int ngroups = (n + gmax - 1) / gmax;
     const int elem = h->fp64 ? 8 : 4;
     const int sms = device_sms();
-    const bool entropic = h->om != OM_FIXED && h->family != FAM_LINEAR2;
-    const int consumers = step2d_threads((int)h->sz.planes / 4, entropic, h->fp64, h->om == OM_MIXED) - 32;
     std::vector<std::pair<int, int>> spans;  // [first, count)
     for (int g = 0, first = 0; g < ngroups; ++g) {
         const int cnt = n / ngroups + (g < n % ngroups ? 1 : 0);
@@ -313,7 +311,7 @@ bool step_groups2d(const eslbm_handle *h, int64_t pending, std::vector<Group2d> 
             G.sl.kind[j] = st[(size_t)(spans[i].first + j)].second;
             G.sl.halo += std::abs(G.sl.shift[j]);
         }
-        if (plan_step2d(h->cfg.nx, h->cfg.ny, (int)h->sz.planes, elem, sms, G.sl, consumers, G.plan)) {
+        if (plan_step2d(h->cfg.nx, h->cfg.ny, (int)h->sz.planes, elem, sms, G.sl, G.plan)) {
             out.push_back(G);
         } else {
             if (G.sl.n == 1) return false;
@@ -627,7 +625,7 @@ eslbm_status eslbm_query(const eslbm_config *cfg, eslbm_sizes *out)
     if (cfg->dim == 1 && cfg->blocking != ESLBM_BLOCKING_OFF) {
         z.launches_per_step = 1.0 / (double)fused_group_of(stages);
     } else if (blocked2d_of(*cfg, z.planes)) {
-        eslbm_handle probe;  // the grouping needs the configuration, sizes, family, omega mode and operator list
+        eslbm_handle probe;  // the grouping needs the configuration, sizes and operator list
         probe.cfg = *cfg;
         probe.sz = z;
         probe.fp64 = cfg->precision == ESLBM_FP64;

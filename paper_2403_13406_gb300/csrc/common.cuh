@@ -131,12 +131,6 @@ struct StageList {
 #ifndef ESLBM_STEP2D_PREFETCH
 #define ESLBM_STEP2D_PREFETCH 3
 #endif
-#ifndef ESLBM_STEP2D_ROWS
-#define ESLBM_STEP2D_ROWS 1
-#endif
-#ifndef ESLBM_STEP2D_NARROW
-#define ESLBM_STEP2D_NARROW 0
-#endif
 #ifndef ESLBM_STEP2D_THREADS
 #define ESLBM_STEP2D_THREADS 768
 #endif
@@ -144,9 +138,7 @@ constexpr int kStep2dThreads = ESLBM_STEP2D_THREADS;             // threads of a
 constexpr int kStep2dSlots = 8;                                   // items (stage, column) a thread owns
 constexpr int kStep2dMaxItems = kStep2dSlots * (256 - 32);        // items of a tick (smallest block: 256)
 constexpr int kStep2dBlocksPerSm = ESLBM_STEP2D_BLOCKS_PER_SM;  // resident blocks per SM (shared memory split)
-constexpr int kStep2dPrefetch = ESLBM_STEP2D_PREFETCH;          // window rows loaded ahead of use (at least)
-constexpr int kStep2dRowsPerTick = ESLBM_STEP2D_ROWS;  // rows a stage advances per tick (1, 2 or 4)
-constexpr bool kStep2dNarrow = ESLBM_STEP2D_NARROW;     // narrow the strip to one cell per consumer when rows > 1
+constexpr int kStep2dPrefetch = ESLBM_STEP2D_PREFETCH;          // window rows loaded ahead of use
 constexpr int kStep2dMaxStages = 32;
 constexpr int kStep2dMaxRing = 64;
 constexpr int kStep2dBarBytes = 8 * kStep2dMaxRing;
@@ -156,27 +148,10 @@ constexpr int kStep2dSmemBudget = 232448 / kStep2dBlocksPerSm - 2048;
 // stages: a block owns tx x ly output cells and keeps `ring` rows of a window
 // tx + 2 hl wide in shared memory (see step2d.cuh).
 struct Plan2d {
-    int tx, ly, hl, wx;
-    int ring;      // rows in the ring (rpt blocks of rows, one mbarrier per block)
-    int prefetch;  // blocks of rows loaded ahead
-    int rpt;       // rows a stage advances per tick
-    int nstrips, nsegs;
-    int items;    // (stage, row, column) items of a tick: rpt times the sum over the stages of tx + 2 (H - m_j)
+    int tx, ly, hl, wx, ring, prefetch, nstrips, nsegs;
+    int items;    // (stage, column) items of a tick: sum over the stages of tx + 2 (H - m_j)
     size_t smem;  // dynamic shared memory bytes
 };
-
-// Threads of a block of the temporally blocked 2D kernel: as many as the registers of the relaxation
-// allow (one block per SM) -- FP32: kStep2dThreads for a fixed omega (or a linear system), 640 for the
-// entropic scalar relaxation, 512 for entropic shallow water and 384 with its FP64 evaluation (the
-// mixed mode); FP64 storage: 512, and 256 for entropic shallow water.
-constexpr int step2d_threads(int M, bool entropic_nonlinear, bool fp64, bool mixed)
-{
-    return !entropic_nonlinear ? (fp64 ? 512 : kStep2dThreads)
-           : M == 1            ? (fp64 ? 512 : 640)
-           : fp64              ? 256
-           : mixed             ? 384
-                               : 512;
-}
 
 inline bool stage_list_ok(const StageList &sl)
 {

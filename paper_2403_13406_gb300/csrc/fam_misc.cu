@@ -281,35 +281,33 @@ int device_sms()
     return sms;
 }
 
-// One candidate plan with R rows per tick: the lags in ticks, the ring that keeps every block until its
-// last reader, the widest strip the shared memory allows and the tick's items.
-static bool plan_rows(int64_t nx, int64_t ny, int planes, int elem, int sms, const StageList &sl, int R,
-                      int items_cap, Plan2d &pl)
+bool plan_step2d(int64_t nx, int64_t ny, int planes, int elem, int sms, const StageList &sl, Plan2d &pl)
 {
+    if (!stage_list_ok(sl) || sl.n > kStep2dMaxStages || planes < 1 || (elem != 4 && elem != 8)) return false;
     const int V4 = 16 / elem;
+    if (nx % V4) return false;
     const int H = sl.halo;
-    int L = 0, acc = 0, EB = 0, m = 0;
+    // lags of the stages behind the load, and the ring that keeps every slot until its last reader
+    int lag = 0, acc = 0, E = 0;
     int64_t items_margin = 0;
+    int m = 0;
     for (int j = 0; j < sl.n; ++j) {
         const int s = sl.shift[j], as = s < 0 ? -s : s;
-        L = (j > 0 ? L + 1 : 0) + (as + R - 1) / R;
+        lag += as + (j > 0 ? 1 : 0);
         acc += s;
         m += as;
-        const int aa = acc < 0 ? -acc : acc;
-        EB = std::max(EB, L + (aa + R - 1) / R);
+        E = std::max(E, lag + (acc < 0 ? -acc : acc));
         items_margin += 2 * (H - m);
     }
-    pl.rpt = R;
-    pl.prefetch = (kStep2dPrefetch + R - 1) / R;
-    const int ringB = EB + pl.prefetch;
-    pl.ring = ringB * R;
+    pl.prefetch = kStep2dPrefetch;
+    pl.ring = E + pl.prefetch;
     if (pl.ring > kStep2dMaxRing) return false;
     pl.hl = (H + V4 - 1) / V4 * V4;
     const int64_t budget = kStep2dSmemBudget - kStep2dBarBytes;
     const int wx_max = (int)(budget / ((int64_t)pl.ring * planes * elem)) / V4 * V4;
     const int tx_max = wx_max - 2 * pl.hl;
-    // a tick's items (about R n tx) within items_cap (at most the slots of the smallest block)
-    const int tx_cap = (int)std::min<int64_t>(tx_max, (items_cap / R - items_margin) / sl.n / V4 * V4);
+    // a tick's items (about n tx) must fit the slots of the smallest block
+    const int tx_cap = (int)std::min<int64_t>(tx_max, (kStep2dMaxItems - items_margin) / sl.n / V4 * V4);
     if (tx_cap < std::max(4 * V4, pl.hl)) return false;
     // strips as wide as the window allows, evened out over the row
     int64_t nstrips = (nx + tx_cap - 1) / tx_cap;
@@ -318,8 +316,7 @@ static bool plan_rows(int64_t nx, int64_t ny, int planes, int elem, int sms, con
     nstrips = (nx + pl.tx - 1) / pl.tx;
     pl.nstrips = (int)nstrips;
     pl.wx = pl.tx + 2 * pl.hl;
-    // rows per block: the time is (waves of kStep2dBlocksPerSm blocks per SM) x (rows a block sweeps,
-    // with the pipeline's fill and drain)
+    // rows per block: the time is (waves of kStep2dBlocksPerSm blocks per SM) x (ticks of a block)
     static const int cand[] = {32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096, 8192};
     double best = 0.0;
     pl.ly = 0;
@@ -328,7 +325,7 @@ static bool plan_rows(int64_t nx, int64_t ny, int planes, int elem, int sms, con
         const int64_t nsegs = (ny + lye - 1) / lye;
         const int64_t blocks = nstrips * nsegs;
         const int64_t waves = (blocks + (int64_t)sms * kStep2dBlocksPerSm - 1) / ((int64_t)sms * kStep2dBlocksPerSm);
-        const double cost = (double)waves * (double)(lye + 2 * H + R * L);
+        const double cost = (double)waves * (double)(lye + H + lag);
         if (pl.ly == 0 || cost < best) {
             best = cost;
             pl.ly = lye;
@@ -337,22 +334,9 @@ static bool plan_rows(int64_t nx, int64_t ny, int planes, int elem, int sms, con
         if (ly >= ny) break;
     }
     if ((int64_t)pl.nstrips * pl.nsegs > 0x7fffffffLL) return false;
-    pl.items = (int)((int64_t)R * (sl.n * (int64_t)pl.tx + items_margin));
+    pl.items = (int)((int64_t)sl.n * pl.tx + items_margin);
     pl.smem = (size_t)kStep2dBarBytes + (size_t)pl.ring * planes * pl.wx * elem;
     return pl.smem <= (size_t)kStep2dSmemBudget;
-}
-
-bool plan_step2d(int64_t nx, int64_t ny, int planes, int elem, int sms, const StageList &sl, int consumers, Plan2d &pl)
-{
-    if (!stage_list_ok(sl) || sl.n > kStep2dMaxStages || planes < 1 || (elem != 4 && elem != 8) || consumers < 32)
-        return false;
-    if (nx % (16 / elem)) return false;
-    // Rows per tick: kStep2dRowsPerTick, a constant of the kernel.  One row per tick measured fastest on
-    // GB300 (Euler 8192^2, two stages a launch: 204 ms for ten steps against 231 ms with two rows a
-    // tick, and 269 ms with two rows and the strip narrowed to one cell per consumer, where the
-    // consumers then waited on the rows' copies); more rows per tick remain a build option.
-    return plan_rows(nx, ny, planes, elem, sms, sl, kStep2dRowsPerTick,
-                     (kStep2dRowsPerTick > 1 && kStep2dNarrow) ? consumers : kStep2dMaxItems, pl);
 }
 
 cudaError_t batch_adjoint_sw2(bool, int, const BatchAdjointLaunch &);

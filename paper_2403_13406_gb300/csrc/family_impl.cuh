@@ -256,13 +256,12 @@ cudaError_t step2d_one(const Step2dLaunch &L)
     if (!stage_list_ok(L.sl) || L.sl.n > kStep2dMaxStages) return cudaErrorInvalidValue;
     const Plan2d &pl = L.plan;
     if (pl.ring > kStep2dMaxRing || pl.smem > (size_t)kStep2dSmemBudget) return cudaErrorInvalidValue;
-    // threads: a producer warp, and as many consumers as the tick has items, up to the variant's
-    // threads (at most kStep2dSlots items a consumer)
+    // threads: a producer warp, and consumers over which the items of a tick spread evenly (at most
+    // the variant's threads in all, at most kStep2dSlots items a consumer)
     constexpr int cmax = Step2dThreads<Sys, R, OM>::value - 32;
-    const int consumers = std::min(cmax, (pl.items + 31) / 32 * 32);
-    const int nslots = (pl.items + consumers - 1) / consumers;
-    if (pl.items < 1 || nslots > kStep2dSlots) return cudaErrorInvalidValue;
-    const int threads = 32 + consumers;
+    const int nslots = (pl.items + cmax - 1) / cmax;
+    if (nslots < 1 || nslots > kStep2dSlots) return cudaErrorInvalidValue;
+    const int threads = 32 + ((pl.items + nslots - 1) / nslots + 31) / 32 * 32;
     static std::atomic<int> attr[kMaxDevices];
     const int d = device_slot();
     if (!attr[d].load()) {
@@ -271,9 +270,8 @@ cudaError_t step2d_one(const Step2dLaunch &L)
         if (e != cudaSuccess) return e;
         attr[d].store(1);
     }
-    if (pl.rpt != kStep2dRowsPerTick || pl.ring % pl.rpt) return cudaErrorInvalidValue;
     Step2dArgs<R> a{(const R *)L.fin, (R *)L.fout, L.nx, L.ny, L.ncell, pl.tx, pl.ly, pl.hl, pl.wx, pl.ring,
-                    pl.prefetch, pl.nstrips, pl.rpt, L.cnt};
+                    pl.prefetch, pl.nstrips, L.cnt};
     const unsigned grid = (unsigned)((int64_t)pl.nstrips * pl.nsegs);
     k_step2d<Sys, R, OM><<<grid, threads, pl.smem, L.stream>>>(a, L.sl, params_as<R>(L.P));
     return cudaGetLastError();

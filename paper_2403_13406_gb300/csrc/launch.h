@@ -50,11 +50,9 @@ struct Step2dLaunch {
 };
 
 // Plan of one launch of the temporally blocked 2D kernel for the stages sl on an
-// nx x ny grid with `planes` planes of `elem`-byte values on `sms` SMs, for a block
-// of `consumers` relaxing threads; false if the stages do not fit (rows not on
-// 16-byte boundaries, ring or window too large).
-bool plan_step2d(int64_t nx, int64_t ny, int planes, int elem, int sms, const StageList &sl, int consumers,
-                 Plan2d &out);
+// nx x ny grid with `planes` planes of `elem`-byte values on `sms` SMs; false if
+// the stages do not fit (rows not on 16-byte boundaries, ring or window too large).
+bool plan_step2d(int64_t nx, int64_t ny, int planes, int elem, int sms, const StageList &sl, Plan2d &out);
 // several fused stages of a 2D lattice in one launch (plan from plan_step2d)
 cudaError_t launch_step2d(int family, bool fp64, int om, const Step2dLaunch &L);
 // SMs of the current device (cached per device)
