@@ -148,3 +148,21 @@ def test_create_rejects_bad_buffers(L):
     st = L.eslbm_create(ctypes.byref(cfg), 17, 48, 64, None, ctypes.byref(h))  # misaligned
     assert st == eslbm.ERR_ARG
     assert L.eslbm_destroy(None) == 0
+
+
+@pytest.mark.parametrize("system,kw,precision,mode,blocking,nx,expected", [
+    # AUTO: two stages a launch of the blocked 2D kernel for the 16-plane Euler state in FP32, fixed omega
+    ("euler", dict(V=8.0, gamma=1.4), "fp32", "fixed", True, 8192, 9.0),
+    ("euler", dict(V=8.0, gamma=1.4), "fp32", "fixed", False, 8192, 18.0),
+    ("euler", dict(V=8.0, gamma=1.4), "fp64", "fixed", True, 8192, 18.0),
+    ("euler", dict(V=8.0, gamma=1.4), "fp32", "fixed", True, 8190, 18.0),  # rows off 16-byte boundaries
+    ("euler", dict(V=8.0, gamma=1.4), "fp32", "fixed", 6, 8192, 3.0),
+    ("burgers", dict(V=3.0), "fp32", "fixed", True, 4096, 18.0),
+    ("burgers", dict(V=3.0), "fp32", "entropic", True, 4096, 18.0),
+    ("sw", dict(V=8.0, g=9.81), "fp32", "entropic", True, 1024, 18.0),
+])
+def test_blocking_choice_in_2d(system, kw, precision, mode, blocking, nx, expected):
+    """Launches per composite step that the library reports for a 2D configuration (no device needed: the
+    grouping of the stages is planned on the host)."""
+    cfg = eslbm.make_config(2, system, nx, nx, precision=precision, omega_mode=mode, blocking=blocking, **kw)
+    assert eslbm.query(cfg).launches_per_step == expected
