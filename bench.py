@@ -152,10 +152,10 @@ def aggregate(total_ms, units_per_rank, dist=None, device=None):
 # DRAM bytes (read + write) per launch of the dominant kernels, from the ncu captures summarised under
 # profiles/ (at a smaller size where noted, scaled by the cells a launch processes)
 TRAFFIC = {
-    "k_step2d_euler_8192_g2": (8.20e9, "profiles/k_step2d_euler_n2048_g2.md: 513 MB at 2048^2, x 16"),
-    "k_stage_bulk_euler_8192": (7.70e9, "profiles/k_stage_bulk_euler_n2048_fp32_fixed.md: 481 MB at 2048^2, x 16"),
-    "k_step1d_sw1d_2^20": (16.8e6, "profiles/k_step1d_sw1d_n1048576_fp32_entropic.md (the writes stay in L2)"),
-    "k_batch_step_sw2d_64": (47.0e9, "profiles/k_batch_step_sw2d_8inst_fp32_entropic.md: 7.18 GB for 4.12 M cells, "
+    "k_step2d_euler_8192_g2": (8.20e9, "profiles/k_step2d_euler_n2048_g2.txt: 513 MB at 2048^2, x 16"),
+    "k_stage_bulk_euler_8192": (7.70e9, "profiles/k_stage_bulk_euler_n2048_fp32_fixed.txt: 481 MB at 2048^2, x 16"),
+    "k_step1d_sw1d_2^20": (16.8e6, "profiles/k_step1d_sw1d_n1048576_fp32_entropic.txt (the writes stay in L2)"),
+    "k_batch_step_sw2d_64": (47.0e9, "profiles/k_batch_step_sw2d_8inst_fp32_entropic.txt: 7.18 GB for 4.12 M cells, "
                                      "x 26.99 M / 4.12 M"),
 }
 
