@@ -403,8 +403,9 @@ def test_full_size_burgers2d_sampled():
 def test_fp32_conservation_over_long_runs(system, dim, n, kw, mode, steps):
     """The relaxation conserves the moments: on D2Q4 the deviation of the last population of each
     component is minus the sum of the others, so the conserved totals move only by the rounding of the
-    relaxed values, unbiased (D1Q2 keeps both deviations; its totals stay within the same bar): after thousands of stages the mass stays within a random walk of the FP32
-    rounding of the state (relative 1e-6), where deviations taken from independently rounded
+    relaxed values, unbiased (D1Q2 keeps both deviations; its totals stay within the same bar): after
+    thousands of stages the mass stays within a random walk of the FP32 rounding of the state
+    (relative 1e-6), where deviations taken from independently rounded
     equilibria drifted by 1.4e-4 over 36 000 stages of 2D Burgers.  (Euler runs scheme III, the
     paper's Euler setting: in FP32 the undamped scheme I at omega = 2 does not stay finite over three
     crossings of the periodic domain at 384^2, while FP64 does.)"""
