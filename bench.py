@@ -154,7 +154,6 @@ def aggregate(total_ms, units_per_rank, dist=None, device=None):
 TRAFFIC = {
     "k_step2d_euler_8192_g2": (8.20e9, "profiles/k_step2d_euler_n2048_g2.txt: 513 MB at 2048^2, x 16"),
     "k_stage_bulk_euler_8192": (7.70e9, "profiles/k_stage_bulk_euler_n2048_fp32_fixed.txt: 481 MB at 2048^2, x 16"),
-    "k_step1d_sw1d_2^20": (16.8e6, "profiles/k_step1d_sw1d_n1048576_fp32_entropic.txt (the writes stay in L2)"),
     "k_batch_step_sw2d_64": (47.0e9, "profiles/k_batch_step_sw2d_8inst_fp32_entropic.txt: 7.18 GB for 4.12 M cells, "
                                      "x 26.99 M / 4.12 M"),
 }
@@ -384,7 +383,7 @@ def sw1d_leg(torch, eslbm, inputs, stream, dev):
                         n_steps, {"alu_view": {"achieved_tflops": flops, "peak_tflops": FP32_PEAK_TFLOPS,
                                                "frac": flops / FP32_PEAK_TFLOPS,
                                                "flops_per_cell_stage": SW_FLOPS_PER_CELL_STAGE}},
-                        traffic="k_step1d_sw1d_2^20" if N == 1 << 20 else None)
+                        traffic=None)  # the capture predates the kernel's current D1Q2 deviations
     return {"sw1d": {"workload": "sw1d_d1q2_entropic_n%d_t%g" % (N, SW_T), "N": N, "V": SW_V, "g": G,
                      "t_final": n_steps * 24.0 / N / SW_V, "composite_steps": n_steps, "ms": ms,
                      "site_updates_per_s": N * n_steps / s, "roofline": roof, "fallbacks": fb,
