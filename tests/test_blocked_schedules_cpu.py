@@ -1,4 +1,5 @@
-"""The index scheme of the temporally blocked 2D kernel (k_step2d), restated on the CPU.
+"""The index schemes of the temporally blocked kernels (k_step2d, and k_step1d at the end), restated on
+the CPU.
 
 A block sweeps a strip of the grid along y with a ring of window rows in shared memory; stage j relaxes
 one row per tick, lagging the load by L_1 = |s_1| and stage j - 1 by |s_j| + 1 rows; population k of
@@ -125,3 +126,64 @@ def test_blocked_schedule_matches_per_stage(shape, shifts, tx_cap, ly):
     p = plan(nx, ny, shifts, tx_cap, ly)
     got = blocked(f, shifts, 1.7, (0.2, -0.15), p)
     assert np.abs(got - per_stage(f, shifts, 1.7, (0.2, -0.15))).max() < 1e-12
+
+
+def fused1d(f, shifts, omega, a, T):
+    """The 1D fused step (k_step1d): a tile of T cells and a window of W = T + 2H cells of every plane in
+    shared memory; population k of window cell x lives at circular slot (x - o_k) mod W, a stage adds
+    sign_k s to o_k and relaxes the cells [m, W - m) in place (m = |s_1| + ... up to this stage), and the
+    tile [H, H + T) is written out."""
+    n = f.shape[1]
+    H = sum(abs(s) for s in shifts)
+    out = np.full_like(f, np.nan)
+    sign = [1, -1]
+    for x0 in range(0, n, T):
+        t = min(T, n - x0)
+        W = t + 2 * H
+        idx = (x0 - H + np.arange(W)) % n
+        val = f[:, idx].copy()
+        tag = [[(k, i, 0) for i in range(W)] for k in range(2)]
+        off, moved = [0, 0], 0
+        for st, s in enumerate(shifts):
+            off = [off[k] + sign[k] * s for k in range(2)]
+            moved += abs(s)
+            new = {}
+            for x in range(moved, W - moved):
+                fv = np.empty(2)
+                for k in range(2):
+                    slot = (x - off[k]) % W
+                    assert tag[k][slot] == (k, x - sign[k] * s, st)
+                    fv[k] = val[k, slot]
+                u = fv.sum()
+                fe = np.array([u / 2 + a * u / 2, u / 2 - a * u / 2])
+                fn = fv + omega * (fe - fv)
+                for k in range(2):
+                    new[(k, (x - off[k]) % W)] = (fn[k], (k, x, st + 1))
+            for (k, slot), (v, tg) in new.items():
+                val[k, slot], tag[k][slot] = v, tg
+        for x in range(H, H + t):
+            for k in range(2):
+                slot = (x - off[k]) % W
+                assert tag[k][slot] == (k, x, len(shifts))
+                out[k, x0 + x - H] = val[k, slot]
+    return out
+
+
+def per_stage_1d(f, shifts, omega, a):
+    f = f.copy()
+    for s in shifts:
+        g = np.stack([np.roll(f[0], s), np.roll(f[1], -s)])
+        u = g.sum(0)
+        fe = np.stack([u / 2 + a * u / 2, u / 2 - a * u / 2])
+        f = g + omega * (fe - g)
+    return f
+
+
+@pytest.mark.parametrize("n,T", [(64, 16), (70, 24), (50, 50)])
+def test_fused1d_schedule_matches_per_stage(n, T):
+    """All 18 stages of a composite step (shifts 1, 2 x 7, -1, -4, -1, 2 x 7) in one window, ragged last
+    tile included."""
+    shifts = [1] + [2] * 7 + [-1, -4, -1] + [2] * 7
+    f = np.random.default_rng(3).standard_normal((2, n))
+    got = fused1d(f, shifts, 1.8, 0.3, T)
+    assert np.abs(got - per_stage_1d(f, shifts, 1.8, 0.3)).max() < 1e-12
